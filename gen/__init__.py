@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs for the k-hop neighbourhood count.
+
+This module makes graphs, seed lists and request streams and nothing else: it
+holds none of the counting method.  The CPU oracle and the CUDA library both
+consume its output, so the two sides always see the same inputs.
+
+Workload shapes follow the paper's benchmark (Sec. III): Graph500-style
+Kronecker (R-MAT) graphs and a Twitter-like power-law graph, 300 seeds for the
+1- and 2-hop queries and 10 seeds for the 3- and 6-hop queries.
+
+The heavy lifting is in ``khopgen.c`` (counter-based splitmix64, R-MAT,
+Fisher-Yates relabelling, CSR build with dedup, Walker alias tables), compiled
+on first use with gcc into ``libkhopgen.so`` next to this file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "khopgen.c")
+_SO = os.path.join(_HERE, "libkhopgen.so")
+_lock = threading.Lock()
+_lib = None
+
+# Stream sub-keys derived from a user seed: draw j of stream `seed`.
+_SUB_EDGES, _SUB_PERM, _SUB_SRC, _SUB_DST, _SUB_WPERM_OUT, _SUB_WPERM_IN = range(6)
+
+
+def build(force: bool = False) -> str:
+    """Compile khopgen.c into libkhopgen.so (portable flags, no -march)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-pthread",
+                        _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            u64, i64, u32p, u64p = ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+            lib.khopgen_rand.restype = u64
+            lib.khopgen_rand.argtypes = [u64, u64]
+            lib.khopgen_unif.restype = ctypes.c_double
+            lib.khopgen_unif.argtypes = [u64, u64]
+            lib.khopgen_rand_fill.argtypes = [u64, u64, u64, u64p]
+            lib.khopgen_rmat_edges.restype = ctypes.c_int
+            lib.khopgen_rmat_edges.argtypes = [ctypes.c_int, u64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, u64, u32p, u32p, ctypes.c_int]
+            lib.khopgen_permutation.argtypes = [u64, u64, u32p]
+            lib.khopgen_relabel.argtypes = [u32p, u32p, u64, ctypes.c_int]
+            lib.khopgen_csr_begin.restype = i64
+            lib.khopgen_csr_begin.argtypes = [u64, u64, u32p, u32p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_void_p)]
+            lib.khopgen_csr_finish.argtypes = [ctypes.c_void_p, u64p, u32p]
+            lib.khopgen_seeds.restype = i64
+            lib.khopgen_seeds.argtypes = [u64, u64p, u64, u64, u32p]
+            lib.khopgen_alias_build.restype = ctypes.c_int
+            lib.khopgen_alias_build.argtypes = [u64, ctypes.c_void_p, ctypes.c_void_p, u32p]
+            lib.khopgen_chunglu_edges.argtypes = [u64, ctypes.c_void_p, u32p, ctypes.c_void_p, u32p,
+                                                  u64, u64, u64, u64, u32p, u32p, ctypes.c_int]
+            lib.khopgen_poisson.argtypes = [u64, ctypes.c_double, u64, ctypes.c_void_p, u32p,
+                                            ctypes.c_int, u64, u32p, ctypes.c_void_p, u32p, u32p]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def rand(key: int, i: int) -> int:
+    """Draw i of the counter-based splitmix64 stream `key` (uint64)."""
+    return int(_L().khopgen_rand(key & (2**64 - 1), i))
+
+
+def rand_array(key: int, start: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.uint64)
+    _L().khopgen_rand_fill(key & (2**64 - 1), start, count, _p(out))
+    return out
+
+
+def subkey(seed: int, j: int) -> int:
+    return rand(seed, j)
+
+
+@dataclass
+class CSRGraph:
+    """A directed graph as CSR: row u lists the heads of the edges u -> w.
+
+    row_ptr is uint64[n+1], col_idx is uint32[nnz].  `symmetric` records that
+    every edge has its reverse (so CSC equals CSR)."""
+    n: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    symmetric: bool = False
+    name: str = ""
+    params: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def out_degree(self) -> np.ndarray:
+        return np.diff(self.row_ptr).astype(np.int64)
+
+    def row_ptr_as(self, width: int) -> np.ndarray:
+        if width == 8:
+            return self.row_ptr
+        if self.nnz >= 2**32:
+            raise ValueError("nnz does not fit 32-bit row_ptr")
+        return self.row_ptr.astype(np.uint32)
+
+
+def csr_from_edges(n: int, src, dst, symmetrize: bool = False, nthreads: int = 0,
+                   name: str = "", params: dict | None = None) -> CSRGraph:
+    """Edge list -> CSR with self-loops removed, optional symmetrisation and
+    duplicate edges collapsed; each row sorted ascending."""
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    if src.shape != dst.shape:
+        raise ValueError("src/dst length mismatch")
+    if src.size and (int(src.max()) >= n or int(dst.max()) >= n):
+        raise ValueError("vertex id out of range")
+    h = ctypes.c_void_p()
+    nnz = _L().khopgen_csr_begin(n, src.size, _p(src), _p(dst), int(symmetrize), nthreads,
+                                 ctypes.byref(h))
+    if nnz < 0:
+        raise MemoryError("csr build failed")
+    row_ptr = np.empty(n + 1, dtype=np.uint64)
+    col = np.empty(max(nnz, 1), dtype=np.uint32)
+    _L().khopgen_csr_finish(h, _p(row_ptr), _p(col))
+    return CSRGraph(n, row_ptr, col[:nnz], symmetrize, name, dict(params or {}))
+
+
+def csr_raw(n: int, src, dst) -> CSRGraph:
+    """Edge list -> CSR keeping duplicates and self-loops, edges of a row in
+    input order (a stable sort by tail)."""
+    src = np.asarray(src, dtype=np.uint64)
+    dst = np.asarray(dst, dtype=np.uint32)
+    order = np.argsort(src, kind="stable")
+    counts = np.bincount(src.astype(np.int64), minlength=n)[:n] if src.size else np.zeros(n, np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.uint64)
+    row_ptr[1:] = np.cumsum(counts)
+    return CSRGraph(n, row_ptr, dst[order].astype(np.uint32), False, "raw", {})
+
+
+def rmat(scale: int, edge_factor: int = 16, A: float = 0.57, B: float = 0.19, C: float = 0.19,
+         seed: int = 1, symmetrize: bool = False, permute: bool = True,
+         nthreads: int = 0) -> CSRGraph:
+    """Graph500-shaped Kronecker (R-MAT) graph on 2^scale vertices.
+
+    edge_factor * 2^scale candidate edges; edge e, level l draws
+    u = draw(e*scale + l) of stream subkey(seed, 0) and picks quadrant
+    (0,0) if u < A, (0,1) if u < A+B, (1,0) if u < A+B+C, else (1,1), most
+    significant bit first.  With `permute`, vertex ids are relabelled by a
+    seeded Fisher-Yates permutation (stream subkey(seed, 1)), as Graph500 does.
+    Self-loops are dropped and duplicates collapsed; `symmetrize` adds every
+    reverse edge first."""
+    n = 1 << scale
+    m = edge_factor * n
+    src = np.empty(m, dtype=np.uint32)
+    dst = np.empty(m, dtype=np.uint32)
+    rc = _L().khopgen_rmat_edges(scale, m, A, B, C, subkey(seed, _SUB_EDGES), _p(src), _p(dst),
+                                 nthreads)
+    if rc != 0:
+        raise ValueError("bad R-MAT parameters")
+    if permute:
+        perm = np.empty(n, dtype=np.uint32)
+        _L().khopgen_permutation(n, subkey(seed, _SUB_PERM), _p(perm))
+        _L().khopgen_relabel(_p(perm), _p(src), m, nthreads)
+        _L().khopgen_relabel(_p(perm), _p(dst), m, nthreads)
+    params = dict(kind="rmat", scale=scale, edge_factor=edge_factor, A=A, B=B, C=C, seed=seed,
+                  symmetrize=symmetrize, permute=permute, candidates=m)
+    name = f"rmat-s{scale}-ef{edge_factor}-seed{seed}{'-sym' if symmetrize else ''}"
+    return csr_from_edges(n, src, dst, symmetrize, nthreads, name, params)
+
+
+def rmat_edges_unpermuted(scale: int, m: int, A=0.57, B=0.19, C=0.19, seed: int = 1):
+    """Raw R-MAT candidate edges before relabelling (for generator checks)."""
+    src = np.empty(m, dtype=np.uint32)
+    dst = np.empty(m, dtype=np.uint32)
+    rc = _L().khopgen_rmat_edges(scale, m, A, B, C, subkey(seed, _SUB_EDGES), _p(src), _p(dst), 0)
+    if rc != 0:
+        raise ValueError("bad R-MAT parameters")
+    return src, dst
+
+
+def permutation(n: int, key: int) -> np.ndarray:
+    perm = np.empty(n, dtype=np.uint32)
+    _L().khopgen_permutation(n, key, _p(perm))
+    return perm
+
+
+def seeds(g: CSRGraph, count: int, seed: int = 2) -> np.ndarray:
+    """`count` seeds drawn uniformly with replacement from the vertices with
+    out-degree > 0: seed i = eligible[floor(u_i * |eligible|)], u_i = draw i
+    of stream `seed` (53-bit uniform)."""
+    out = np.zeros(count, dtype=np.uint32)
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.uint64)
+    ne = _L().khopgen_seeds(g.n, _p(rp), count, seed, _p(out))
+    if ne < 0:
+        raise MemoryError
+    if ne == 0 and count:
+        raise ValueError("graph has no vertex with out-degree > 0")
+    return out
+
+
+def mixed_ks(count: int, choices=(1, 2, 3, 6), seed: int = 2, stream: int = 7) -> np.ndarray:
+    """k values drawn uniformly from `choices` (stream subkey(seed, stream))."""
+    r = rand_array(subkey(seed, stream), 0, count)
+    idx = ((r >> np.uint64(11)).astype(np.float64) * 2.0**-53 * len(choices)).astype(np.int64)
+    idx = np.minimum(idx, len(choices) - 1)
+    return np.asarray(choices, dtype=np.uint32)[idx]
+
+
+def poisson_stream(g: CSRGraph, count: int, rate_qps: float, seed: int = 3,
+                   k_probs=((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))):
+    """Open-loop request stream: arrival times (s) with exponential gaps of
+    mean 1/rate, k drawn from k_probs, seeds uniform over out-degree > 0."""
+    rp = g.row_ptr
+    eligible = np.nonzero(rp[1:] > rp[:-1])[0].astype(np.uint32)
+    vals = np.asarray([k for k, _ in k_probs], dtype=np.uint32)
+    cdf = np.cumsum([p for _, p in k_probs]).astype(np.float64)
+    t = np.empty(count, dtype=np.float64)
+    ks = np.empty(count, dtype=np.uint32)
+    sd = np.empty(count, dtype=np.uint32)
+    _L().khopgen_poisson(count, float(rate_qps), seed, _p(cdf), _p(vals), len(vals),
+                         eligible.size, _p(eligible), _p(t), _p(ks), _p(sd))
+    return t, ks, sd
+
+
+# --------------------------------------------------------------------------
+# Small named graphs (test fixtures with closed-form answers).
+
+def path_graph(n: int) -> CSRGraph:
+    s = np.arange(max(n - 1, 0), dtype=np.uint32)
+    return csr_from_edges(n, s, s + 1, name=f"path{n}")
+
+
+def cycle_graph(n: int) -> CSRGraph:
+    s = np.arange(n, dtype=np.uint32)
+    return csr_from_edges(n, s, (s + 1) % n, name=f"cycle{n}")
+
+
+def out_star(leaves: int) -> CSRGraph:
+    d = np.arange(1, leaves + 1, dtype=np.uint32)
+    return csr_from_edges(leaves + 1, np.zeros(leaves, np.uint32), d, name=f"ostar{leaves}")
+
+
+def sym_star(leaves: int) -> CSRGraph:
+    d = np.arange(1, leaves + 1, dtype=np.uint32)
+    return csr_from_edges(leaves + 1, np.zeros(leaves, np.uint32), d, symmetrize=True,
+                          name=f"sstar{leaves}")
+
+
+def complete_graph(n: int) -> CSRGraph:
+    a, b = np.meshgrid(np.arange(n, dtype=np.uint32), np.arange(n, dtype=np.uint32), indexing="ij")
+    return csr_from_edges(n, a.ravel(), b.ravel(), name=f"complete{n}")
+
+
+def empty_graph(n: int) -> CSRGraph:
+    return CSRGraph(n, np.zeros(n + 1, np.uint64), np.zeros(0, np.uint32), True, f"empty{n}", {})
+
+
+def disjoint_union(graphs) -> CSRGraph:
+    """Vertex-disjoint union; graph i's vertices are offset by the sizes before it."""
+    rps, cols, off_v, off_e = [np.zeros(1, np.uint64)], [], 0, 0
+    for g in graphs:
+        rps.append(g.row_ptr[1:] + np.uint64(off_e))
+        cols.append(g.col_idx + np.uint32(off_v))
+        off_v += g.n
+        off_e += g.nnz
+    col = np.concatenate(cols) if cols else np.zeros(0, np.uint32)
+    return CSRGraph(off_v, np.concatenate(rps), col.astype(np.uint32),
+                    all(g.symmetric for g in graphs), "union", {})
