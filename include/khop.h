@@ -1,0 +1,253 @@
+/*
+ * khop.h -- C ABI of libkhop, a GB300 (sm_103a) library for the k-hop
+ * neighbourhood count.
+ *
+ * The operation.  RedisGraph (Cailliau et al., "RedisGraph GraphBLAS Enabled
+ * Graph Database", Sec. II) keeps a graph as a sparse Boolean adjacency matrix
+ * A (A[i][j] = 1 for an edge i -> j) and runs traversals as sparse linear
+ * algebra; its benchmark query (Sec. III) is the k-hop neighbourhood count,
+ * k = 1, 2, 3 and 6.  For a seed s this library returns
+ *
+ *     count(s, k) = | { u != s : u is reachable from s in 1..k hops } |
+ *
+ * computed GraphBLAS-style: q0 = v0 = {s}; for r = 1..k
+ *     q_r = (A^T q_{r-1}) AND NOT v_{r-1}      over the (OR, AND) semiring
+ *     v_r = v_{r-1} OR q_r
+ * and count = popcount(v_k) - 1.  All arithmetic is integer: results are exact.
+ *
+ * Conventions for every call:
+ *  - Each call returns a khop_status; nothing aborts the process or traps the
+ *    GPU.  khop_strerror() gives a message.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take device buffers are asynchronous and ordered on
+ *    that stream; the caller synchronises.
+ *  - A graph's traversal state is shared by the calls made on it: calls on one
+ *    graph run one after another (the library orders calls made on different
+ *    streams with events).  Different graphs are independent.
+ *  - Device-side failures (a seed >= n, a device wait that ran out) are
+ *    recorded in the graph's sticky error word, read by khop_get_error().
+ */
+#ifndef KHOP_H
+#define KHOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+enum khop_status {
+    KHOP_OK = 0,
+    KHOP_EINVAL = 1,      /* bad argument (NULL, size, flag, malformed CSR)   */
+    KHOP_ENOMEM = 2,      /* device or host allocation failed                 */
+    KHOP_ECUDA = 3,       /* a CUDA runtime call failed                        */
+    KHOP_EBUSY = 4,       /* admission refused: no memory or slot right now    */
+    KHOP_ETIMEDOUT = 5,   /* a bounded device or host wait ran out             */
+    KHOP_ESHUTDOWN = 6,   /* the server is shutting down                       */
+    KHOP_EDEVICE = 7      /* a device-side error was recorded (khop_get_error) */
+};
+
+/* Sticky device error bits reported by khop_get_error(). */
+enum khop_device_error {
+    KHOP_DEVERR_TIMEOUT = 1,   /* a grid barrier or device wait gave up        */
+    KHOP_DEVERR_SEED = 2,      /* a seed was >= n (its count is UINT64_MAX)   */
+    KHOP_DEVERR_CAPACITY = 4   /* an internal capacity check failed           */
+};
+
+const char *khop_strerror(int status);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int khop_version(void);
+
+/* ---- graphs ------------------------------------------------------------ */
+typedef struct khop_graph khop_graph;
+
+enum khop_graph_flags {
+    KHOP_HOST_PTRS = 0,     /* row_ptr / col_idx are host pointers             */
+    KHOP_DEVICE_PTRS = 1,   /* row_ptr / col_idx are device pointers           */
+    KHOP_SYMMETRIC = 2,     /* caller asserts A = A^T; the CSC is the CSR       */
+    KHOP_VALIDATE = 4,      /* check the CSR (monotone row_ptr, row_ptr[n] =
+                               nnz, col_idx < n) before use; EINVAL if not      */
+    KHOP_WIDE_OFFSETS = 8   /* keep 64-bit edge offsets on the device even when
+                               nnz < 2^32 (otherwise they are stored 32-bit)    */
+};
+
+/*
+ * Create a graph from CSR: row u lists the heads w of the edges u -> w (the
+ * rows of the adjacency matrix A).  The transpose A^T (CSC, in-edges) is
+ * derived on the device.
+ *   n              vertices, 1 <= n < 2^32 (col_idx is 32-bit)
+ *   row_ptr        n+1 offsets, each row_ptr_bytes wide (4 or 8)
+ *   col_idx        nnz uint32 column indices, each < n
+ *   nnz            row_ptr[n]; bitlen(n) + bitlen(nnz) must be <= 64
+ *   flags          khop_graph_flags
+ *   stream         stream for the upload and the derivation
+ *   out            receives the graph handle
+ * Ownership: the inputs are copied and the call synchronises `stream` before
+ * it returns, so the caller may free them when it returns.  The graph owns its device copies and its
+ * traversal state.  Duplicate edges and self-loops are allowed and do not
+ * change any count.
+ * Errors: EINVAL (n, nnz, width, flags, NULL, or a failed KHOP_VALIDATE),
+ * ENOMEM, ECUDA.
+ */
+int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes,
+                      const uint32_t *col_idx, uint64_t nnz, uint32_t flags,
+                      void *stream, khop_graph **out);
+
+/* Free the graph and everything it owns (synchronises the device first). */
+int khop_graph_destroy(khop_graph *g);
+
+/* n and nnz of the graph (either pointer may be NULL). */
+int khop_graph_info(const khop_graph *g, uint64_t *n, uint64_t *nnz);
+
+/* Device memory held by the graph, in bytes (CSR, CSC and state pools). */
+int khop_graph_device_bytes(const khop_graph *g, uint64_t *bytes);
+
+/* ---- traversal tuning -------------------------------------------------- */
+enum khop_direction {
+    KHOP_DIR_AUTO = 0,   /* Beamer direction switch (push <-> pull)          */
+    KHOP_DIR_PUSH = 1,   /* every round expands the frontier (SpMSpV)        */
+    KHOP_DIR_PULL = 2    /* every round scans unvisited vertices (masked SpMV) */
+};
+
+/*
+ * Tunables of a graph.  The direction switch follows Beamer, Asanovic and
+ * Patterson, "Direction-optimizing breadth-first search" (SC 2012): switch
+ * push -> pull when m_f > m_u / alpha and pull -> push when n_f < n / beta,
+ * where n_f is the frontier size, m_f the out-edges of the frontier and m_u
+ * the out-edges of unvisited vertices.  Fields set to 0 keep the current
+ * value.  Changing the tuning never changes a count.
+ */
+typedef struct {
+    int32_t direction;        /* khop_direction                                   */
+    float alpha;              /* push -> pull threshold (> 0)                     */
+    float beta;               /* pull -> push threshold (> 0)                     */
+    int32_t block_threads;    /* threads per CTA of the traversal kernels: 256, 512 or 1024 */
+    int32_t blocks_per_sm;    /* CTAs per SM (capped by occupancy)                */
+    int32_t push_tile;        /* edges per push tile: power of two, 256 .. 8192   */
+    float batch_alpha;        /* alpha for the 64-lane batched traversal          */
+    float batch_beta;         /* beta for the 64-lane batched traversal           */
+} khop_tuning;
+
+int khop_graph_get_tuning(const khop_graph *g, khop_tuning *t);
+int khop_graph_set_tuning(khop_graph *g, const khop_tuning *t);
+
+/*
+ * Pick tuning values for this graph by timing candidate settings on `nq`
+ * seeds (device array `seeds`, k = `k`), keeping the fastest, and apply them.
+ * Synchronises `stream`.  Never changes a count.
+ */
+int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, uint32_t k,
+                  void *stream, khop_tuning *chosen);
+
+/* ---- counting ---------------------------------------------------------- */
+/*
+ * k-hop counts for nseeds seeds with the same k, on the plain single-query
+ * path: the queries run one after another, each over the whole GPU
+ * (direction-optimizing push/pull), inside one persistent launch.
+ *   seeds        device uint32[nseeds]
+ *   k            hops; k = 0 gives 0; large k is fine (stops when the
+ *                frontier empties)
+ *   out_counts   device uint64[nseeds]; a seed >= n gives UINT64_MAX and sets
+ *                KHOP_DEVERR_SEED
+ * Errors: EINVAL, ECUDA.  Asynchronous on `stream`.
+ */
+int khop_count(khop_graph *g, const uint32_t *seeds, uint64_t nseeds, uint32_t k,
+               uint64_t *out_counts, void *stream);
+
+enum khop_mode {
+    KHOP_MODE_AUTO = 0,       /* batched for nseeds >= 2, else plain              */
+    KHOP_MODE_PLAIN = 1,      /* one query at a time                              */
+    KHOP_MODE_BATCHED64 = 2   /* up to 64 queries share one bit-sliced traversal  */
+};
+
+/*
+ * Per-seed k (ks[i] for seeds[i]).  In KHOP_MODE_BATCHED64 the queries are
+ * grouped by k and packed 64 per uint64 lane word; every lane's result equals
+ * the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
+ */
+int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
+                     uint64_t nseeds, uint64_t *out_counts, int mode, void *stream);
+
+/* Per-query record of the plain path (device memory, filled by khop_count_ex). */
+typedef struct {
+    uint64_t t_start_ns;   /* %globaltimer when the query's first round began  */
+    uint64_t t_end_ns;     /* %globaltimer when its count was final           */
+    uint64_t te;           /* TE(s,k): sum of out-degrees of vertices at distance < k */
+    uint64_t bytes;        /* algorithmic HBM bytes of the rounds it ran       */
+    uint32_t rounds;       /* rounds run (<= k; fewer if the frontier emptied) */
+    uint32_t pull_mask;    /* bit r-1 set if round r ran as pull (r <= 32)    */
+} khop_query_stats;
+
+/*
+ * khop_count with per-seed k and optional outputs of the plain path:
+ *   out_te      device uint64[nseeds] or NULL: TE(s, k)
+ *   out_stats   device khop_query_stats[nseeds] or NULL
+ *   per_hop     device uint64[nseeds * hop_stride] or NULL: per_hop[i*stride + r]
+ *               = vertices at distance exactly r (r = 0..min(k, stride-1))
+ */
+int khop_count_ex(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nseeds,
+                  uint64_t *out_counts, uint64_t *out_te, khop_query_stats *out_stats,
+                  uint64_t *per_hop, uint32_t hop_stride, void *stream);
+
+/* Read and clear the graph's sticky device error bits (synchronises the device). */
+int khop_get_error(khop_graph *g, uint32_t *device_error_bits);
+
+/* ---- serving ----------------------------------------------------------- */
+/*
+ * A request server: k-hop queries of mixed k arrive one by one on resident
+ * graphs and are continuously batched: at every round boundary free lanes of
+ * the 64-lane bit-sliced batches take waiting requests, each lane keeps its
+ * own round counter, and a lane retires (its count is final) after its k-th
+ * round.  Batch state is admitted by free device memory.  This is the GPU
+ * counterpart of the paper's thread pool serving many concurrent queries at
+ * low latency (Sec. II).
+ */
+typedef struct khop_server khop_server;
+
+typedef struct {
+    uint64_t mem_budget_bytes;   /* max device bytes for batch state (0 = no cap
+                                    beyond free memory minus a 1 GiB margin)   */
+    uint32_t max_batches;        /* max 64-lane batches per graph (0 = 8)       */
+    int64_t wait_timeout_us;     /* bound for the worker's device waits (0 = 2 s) */
+    uint32_t max_pending;        /* max queued requests before EBUSY (0 = 1<<20) */
+} khop_server_opts;
+
+typedef struct {
+    uint64_t ticket;        /* as returned by khop_submit                      */
+    uint64_t count;         /* the k-hop count (UINT64_MAX on error)           */
+    int32_t status;         /* khop_status of this request                     */
+    uint32_t k;             /* hops requested                                  */
+    uint64_t t_submit_ns;   /* host CLOCK_MONOTONIC at submit                  */
+    uint64_t t_done_ns;     /* host CLOCK_MONOTONIC when the result was posted */
+} khop_result;
+
+/* Create a server (starts its worker thread).  opts may be NULL. */
+int khop_server_create(const khop_server_opts *opts, khop_server **out);
+
+/*
+ * Queue one request: count(seed, k) on graph g (g must outlive the server's
+ * use of it).  Thread-safe.  Errors: EINVAL (seed >= n), EBUSY (queue full),
+ * ESHUTDOWN.
+ */
+int khop_submit(khop_server *s, khop_graph *g, uint32_t seed, uint32_t k, uint64_t *ticket);
+
+/*
+ * Take up to `max` finished results, waiting up to timeout_us (0 = do not
+ * wait, < 0 = wait until at least one is available or the server stops).
+ * *nout receives the number written.  Thread-safe.
+ */
+int khop_poll(khop_server *s, khop_result *out, uint32_t max, uint32_t *nout, int64_t timeout_us);
+
+/* Server counters (any pointer may be NULL). */
+int khop_server_stats(khop_server *s, uint64_t *submitted, uint64_t *completed,
+                      uint64_t *steps, uint64_t *batches_allocated);
+
+/* Stop the worker; requests not finished are completed with ESHUTDOWN. */
+int khop_server_destroy(khop_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHOP_H */
