@@ -1,11 +1,688 @@
-// Bit-sliced 64-lane batched k-hop count (placeholder until the kernel lands).
+// Bit-sliced 64-lane batched k-hop count.
+//
+// Up to 64 queries share one traversal: every vertex v carries three 64-bit
+// lane words -- V[v] (lanes that have visited v), F_in[v] / F_out[v] (lanes
+// whose frontier holds v this round / next round) -- so the (OR, AND)
+// semiring of the single query becomes bitwise OR/AND on lane words:
+//     F_out[w] = (OR over edges u -> w of F_in[u]) AND NOT V[w] AND active
+// where `active` holds the lanes whose k has not been reached.  Lane j's count
+// is the number of set j-bits of V at the end, minus its seed.
+//
+// Queries are grouped on the device into batches of 64 by k (a counting sort
+// by min(k, 63)), so the lanes of a batch mostly finish together.  One
+// cooperative persistent launch then runs every batch: rounds of push
+// (union-frontier queue, 64-bit atomicOr on V and F_out) or pull (lane-mask
+// OR over the in-edges of every vertex some active lane has not visited, with
+// an early exit once all those lanes are covered), chosen by a Beamer-style
+// switch on the union frontier; then a harvest sweep counts the lane bits of
+// V with bit-sliced counters and clears V for the next batch.
+#include <algorithm>
+#include <cmath>
+
 #include "khop_internal.cuh"
 
 namespace khop {
+namespace {
 
-int batch_launch(khop_graph *, const uint32_t *, const uint32_t *, uint64_t, uint64_t *,
-                 cudaStream_t) {
-    return KHOP_EINVAL;
+enum { DIR_PUSH = 0, DIR_PULL = 1 };
+
+constexpr int kBuckets = 64;         // batches are formed per bucket min(k, 63)
+constexpr int kBlock = 512;          // threads per CTA of the batched kernels
+constexpr int kPushUnroll = 4;
+constexpr int kFlatILP = 4;
+constexpr int kPlanes = 8;           // bit-sliced counter planes (up to 255 additions)
+constexpr int kStage = 2048;
+constexpr int kStagePosShift = 40;
+constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+template <typename E>
+struct BatchArgs {
+    uint64_t n, nnz;
+    uint32_t nw;
+    int symmetric;
+    const E *rp;
+    const uint32_t *ci;
+    const E *cp;
+    const uint32_t *ri;
+    const uint32_t *noin;
+    unsigned long long *V;
+    unsigned long long *F0, *F1, *F2;
+    uint32_t *Q0, *Q1;           // union-frontier queue: vertex ids
+    E *Qpre0, *Qpre1;            // queue: out-edge prefix
+    uint32_t *TF0, *TF1;         // first queue item of each push tile
+    CtlBlock *ctl;
+    unsigned long long *part;    // per-CTA lane counts [2][grid][64], by batch parity
+    const uint32_t *seeds;
+    const uint32_t *ks;
+    uint64_t *out;
+    const uint32_t *order;       // 64 query indices per batch (kEmpty = unused lane)
+    const unsigned long long *nbatches;
+    float alpha, beta;
+    uint32_t tile_log2, ebits;
+    int stage;
+    uint64_t pull_cap;
+    uint64_t timeout_ns;
+};
+
+template <typename T>
+__device__ __forceinline__ T sel3(T x0, T x1, T x2, unsigned i) {
+    return i == 0 ? x0 : (i == 1 ? x1 : x2);
+}
+
+struct Shared {
+    unsigned long long cnt, mf, stage, limit, gbase;
+    unsigned long long skipped;  // items not queued because the queue was past its cap
+    int qfull;                   // this CTA saw the queue past its cap (pull rounds)
+    unsigned long long slot[4];
+    int flag;
+    // lane table of the current batch
+    uint32_t seed[64];
+    uint32_t k[64];
+    uint32_t qi[64];
+    unsigned long long deg_pre[65];   // round 1: exclusive prefix of the seeds' out-degrees
+    uint32_t kmax;
+};
+
+template <typename E>
+struct Round {
+    bool first, last;
+    unsigned long long act;      // lanes still running this round
+    const unsigned long long *Fin;
+    unsigned long long *Fout;
+    const uint32_t *Q_in;
+    const E *Qpre_in;
+    const uint32_t *TF_in;
+    uint32_t *Q_out;
+    E *Qpre_out;
+    uint32_t *TF_out;
+    unsigned long long *qpack_out;
+    uint64_t cap, items_in, mf;
+};
+
+template <typename E>
+__device__ __forceinline__ void put_item(const BatchArgs<E> &a, const Round<E> &R, uint64_t pos,
+                                         uint64_t pre, uint32_t w, E d) {
+    if (pos >= R.cap) return;
+    R.Q_out[pos] = w;
+    R.Qpre_out[pos] = (E)pre;
+    const uint64_t jf = (pre + (1ull << a.tile_log2) - 1ull) >> a.tile_log2;
+    const uint64_t jl = (pre + (uint64_t)d - 1ull) >> a.tile_log2;
+    for (uint64_t j = jf; j <= jl; ++j) R.TF_out[j] = (uint32_t)pos;
+}
+
+// Warp-collective: `isnew` marks a lane whose vertex w just entered the union
+// frontier (with out-degree d > 0).  Union counts and out-edge sums go to the
+// CTA; unless this is the last round w joins the next queue through the
+// CTA's shared staging area (as in the single-query kernel).
+template <typename E>
+__device__ __forceinline__ void record(const BatchArgs<E> &a, const Round<E> &R, bool isnew,
+                                       uint32_t w, E d, Shared &sh, uint32_t *st_w, E *st_pre,
+                                       E *st_d) {
+    const unsigned m = __ballot_sync(FULL, isnew);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const E dd = isnew ? d : (E)0;
+    const E incl = warp_inclusive_sum(dd);
+    const E tot = __shfl_sync(FULL, incl, 31);
+    if (lane == 0) {
+        atomicAdd(&sh.cnt, (unsigned long long)__popc(m));
+        atomicAdd(&sh.mf, (unsigned long long)tot);
+    }
+    if (R.last) return;
+    const int leader = __ffs(m) - 1;
+    const unsigned c = __popc(m);
+    const uint64_t rank = (uint64_t)__popc(m & lanemask_lt());
+    const uint64_t excl = (uint64_t)(incl - dd);
+    unsigned long long old = 0;
+    bool staged = false;
+    if (a.stage) {
+        if (lane == leader) {
+            old = atomicAdd(&sh.stage, ((unsigned long long)c << kStagePosShift) + (unsigned long long)tot);
+            if ((old >> kStagePosShift) + c > (unsigned long long)kStage) atomicMin(&sh.limit, old);
+        }
+        old = __shfl_sync(FULL, old, leader);
+        staged = (old >> kStagePosShift) + c <= (unsigned long long)kStage;
+    }
+    const int qfull = __shfl_sync(FULL, *(volatile int *)&sh.qfull, 0);   // warp-uniform
+    if (staged) {
+        if (isnew) {
+            const uint64_t p = (old >> kStagePosShift) + rank;
+            st_w[p] = w;
+            st_pre[p] = (E)((old & kStageEdgeMask) + excl);
+            st_d[p] = d;
+        }
+    } else if (qfull) {
+        // A pull round whose queue is already past its cap: the next round
+        // pulls too, so only the item count is kept.
+        if (lane == leader) atomicAdd(&sh.skipped, (unsigned long long)c);
+    } else {
+        if (lane == leader) {
+            old = atomicAdd(R.qpack_out, ((unsigned long long)c << a.ebits) + (unsigned long long)tot);
+            if ((old >> a.ebits) + c > R.cap) sh.qfull = 1;
+        }
+        old = __shfl_sync(FULL, old, leader);
+        if (isnew)
+            put_item(a, R, (old >> a.ebits) + rank, (old & ((1ull << a.ebits) - 1ull)) + excl, w, d);
+    }
+}
+
+template <typename E>
+__device__ __forceinline__ void flush_round(const BatchArgs<E> &a, const Round<E> &R, Shared &sh,
+                                            uint32_t *st_w, E *st_pre, E *st_d,
+                                            unsigned long long *slot_out) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long st = sh.stage;
+        if (sh.limit < st) st = sh.limit;
+        const uint32_t nst = (uint32_t)(st >> kStagePosShift);
+        if (nst)
+            sh.gbase = atomicAdd(R.qpack_out, ((unsigned long long)nst << a.ebits) +
+                                                  (st & kStageEdgeMask));
+        if (sh.skipped) atomicAdd(R.qpack_out, sh.skipped << a.ebits);
+        sh.skipped = 0;
+        sh.qfull = 0;
+        if (sh.cnt) atomicAdd(slot_out + 1, sh.cnt);
+        if (sh.mf) atomicAdd(slot_out + 3, sh.mf);
+        sh.cnt = sh.mf = 0;
+        sh.stage = 0;
+        sh.limit = ~0ull;
+        sh.flag = (int)nst;
+    }
+    __syncthreads();
+    const uint32_t nst = (uint32_t)sh.flag;
+    if (nst) {
+        const uint64_t gpos = sh.gbase >> a.ebits;
+        const uint64_t gpre = sh.gbase & ((1ull << a.ebits) - 1ull);
+        for (uint32_t t = threadIdx.x; t < nst; t += kBlock)
+            put_item(a, R, gpos + t, gpre + (uint64_t)st_pre[t], st_w[t], st_d[t]);
+    }
+}
+
+// Visit w for the lanes in m: returns true if w entered the union frontier
+// (its first frontier lane this round) and has out-edges; d = out-degree.
+template <typename E>
+__device__ __forceinline__ bool visit(const BatchArgs<E> &a, const Round<E> &R, uint32_t w,
+                                      unsigned long long m, E &d) {
+    const unsigned long long x = m & ~a.V[w];
+    if (!x) return false;
+    const unsigned long long nb = x & ~atomicOr(&a.V[w], x);
+    if (!nb || R.last) return false;
+    d = a.rp[w + 1] - a.rp[w];
+    if (d == 0) return false;   // a frontier vertex without out-edges is never read
+    return atomicOr(&R.Fout[w], nb) == 0ull;
+}
+
+// Push round.  Round 1 expands the lanes' seeds straight from the lane table
+// (item t = lane t, mask = its bit; a self-loop at the seed is skipped); later
+// rounds expand the union-frontier queue with each item's lanes F_in[u] & act.
+template <typename E>
+__device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E> &R, E *s_pre,
+                                           E *s_rs, unsigned long long *s_fm, uint32_t *s_u,
+                                           Shared &sh, uint32_t *st_w, E *st_pre, E *st_d) {
+    const uint32_t tl = a.tile_log2;
+    const uint64_t T = 1ull << tl;
+    const uint64_t ntiles = (R.mf + T - 1) >> tl;
+    for (uint64_t j = blockIdx.x; j < ntiles; j += gridDim.x) {
+        const uint64_t e0 = j << tl;
+        const uint64_t e1 = min(e0 + T, R.mf);
+        uint32_t nitems;
+        if (R.first) {
+            nitems = 64;
+            if (threadIdx.x < 64) {
+                const int l = threadIdx.x;
+                const bool on = sh.qi[l] != kEmpty && ((R.act >> l) & 1ull);
+                s_pre[l] = (E)sh.deg_pre[l];
+                s_rs[l] = on ? a.rp[sh.seed[l]] : (E)0;
+                s_fm[l] = on ? (1ull << l) : 0ull;
+                s_u[l] = on ? sh.seed[l] : kEmpty;
+            }
+        } else {
+            const uint64_t i0 = R.TF_in[j];
+            const uint64_t il = (j + 1 < ntiles) ? (uint64_t)R.TF_in[j + 1] : R.items_in - 1;
+            nitems = (uint32_t)(il - i0 + 1);
+            for (uint32_t t = threadIdx.x; t < nitems; t += kBlock) {
+                const uint32_t u = R.Q_in[i0 + t];
+                s_pre[t] = R.Qpre_in[i0 + t];
+                s_rs[t] = a.rp[u];
+                s_fm[t] = R.Fin[u] & R.act;
+                s_u[t] = kEmpty;
+            }
+        }
+        __syncthreads();
+        uint32_t hint = 0;
+        for (uint64_t base = e0; base < e1; base += (uint64_t)kBlock * kPushUnroll) {
+            uint32_t w[kPushUnroll];
+            unsigned long long m[kPushUnroll];
+#pragma unroll
+            for (int u = 0; u < kPushUnroll; ++u) {
+                const uint64_t e = base + (uint64_t)u * kBlock + threadIdx.x;
+                w[u] = 0;
+                m[u] = 0;
+                if (e < e1) {
+                    uint32_t lo = hint, hi = nitems - 1;   // largest item with prefix <= e
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if ((uint64_t)s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+                    }
+                    hint = lo;
+                    m[u] = s_fm[lo];
+                    if (m[u]) {
+                        w[u] = a.ci[(uint64_t)s_rs[lo] + (e - (uint64_t)s_pre[lo])];
+                        if (w[u] == s_u[lo]) m[u] = 0;   // round 1: a seed's self-loop
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPushUnroll; ++u) {
+                E d = 0;
+                const bool isnew = m[u] && visit(a, R, w[u], m[u], d);
+                record(a, R, isnew, w[u], d, sh, st_w, st_pre, st_d);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pull round: thread per vertex.  need = act & ~V[v]; the vertex ORs the
+// frontier lanes F_in[u] of its in-neighbours until every needed lane is
+// covered.  The first two in-edges are checked by the vertex's own lane;
+// the rest of the still-unresolved in-edge lists of a warp are scanned as
+// one flattened list, the hits OR-ed into a per-warp shared accumulator.
+template <typename E>
+__device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E> &R, Shared &sh,
+                                           E *s_winc, E *s_wpos, unsigned long long *s_acc,
+                                           uint32_t *st_w, E *st_pre, E *st_d) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    E *winc = s_winc + wib * 32;
+    E *wpos = s_wpos + wib * 32;
+    unsigned long long *wacc = s_acc + wib * 32;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
+    for (uint64_t i = gwarp; i < a.nw; i += nwarps) {
+        const uint64_t v = (i << 5) + (uint64_t)lane;
+        const uint32_t ni = a.noin[i];
+        unsigned long long need = 0;
+        if (v < a.n && !((ni >> lane) & 1u)) need = R.act & ~a.V[v];
+        if (__ballot_sync(FULL, need != 0ull) == 0u) {
+            if (v < a.n) R.Fout[v] = 0ull;
+            continue;
+        }
+        E b = 0, e = 0;
+        if (need) {
+            b = a.cp[v];
+            e = a.cp[v + 1];
+        }
+        unsigned long long acc = 0;
+        E pos = b;
+        {
+            const bool l0 = need && pos < e, l1 = l0 && pos + 1 < e;
+            const uint32_t u0 = l0 ? a.ri[pos] : 0u, u1 = l1 ? a.ri[pos + 1] : 0u;
+            if (l0) acc |= R.Fin[u0];
+            if (l1) acc |= R.Fin[u1];
+            pos += (E)l0 + (E)l1;
+        }
+        E rem = (need && (acc & need) != need) ? e - pos : (E)0;
+        while (__any_sync(FULL, rem > 0)) {
+            const E incl = warp_inclusive_sum(rem);
+            const E total = __shfl_sync(FULL, incl, 31);
+            const E excl = incl - rem;
+            winc[lane] = incl;
+            wpos[lane] = pos - excl;
+            wacc[lane] = 0ull;
+            __syncwarp();
+            const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
+            uint32_t uu[kFlatILP];
+            int own[kFlatILP];
+#pragma unroll
+            for (int t = 0; t < kFlatILP; ++t) {
+                const uint32_t x = (uint32_t)(t * 32 + lane);
+                own[t] = -1;
+                uu[t] = 0;
+                if (x < chunk) {
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
+                    }
+                    own[t] = lo;
+                    uu[t] = a.ri[wpos[lo] + (E)x];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kFlatILP; ++t)
+                if (own[t] >= 0) {
+                    const unsigned long long f = R.Fin[uu[t]];
+                    if (f) atomicOr(&wacc[own[t]], f);
+                }
+            __syncwarp();
+            acc |= wacc[lane];
+            const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
+            pos += consumed;
+            rem -= consumed;
+            if ((acc & need) == need) rem = 0;
+            __syncwarp();
+        }
+        const unsigned long long nb = acc & need;
+        if (v < a.n) {
+            R.Fout[v] = nb;
+            if (nb) a.V[v] |= nb;
+        }
+        E d = 0;
+        if (nb && !R.last) d = a.symmetric ? e - b : a.rp[v + 1] - a.rp[v];
+        record(a, R, nb != 0ull && d > 0, (uint32_t)v, d, sh, st_w, st_pre, st_d);
+    }
+}
+
+// Harvest: per-lane popcount of V over all vertices (bit-sliced counters per
+// thread, flushed with warp ballots), written to this CTA's row of `part`;
+// V is cleared on the way.
+__device__ __forceinline__ void harvest(unsigned long long *V, uint64_t n,
+                                        unsigned long long *part_row, unsigned *s_lane) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 64) s_lane[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t iters = (n + gthreads - 1) / gthreads;   // uniform across the CTA
+    unsigned long long p[kPlanes];
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) p[i] = 0ull;
+    for (uint64_t it = 0; it < iters; ++it) {
+        const uint64_t v = gtid + it * gthreads;
+        unsigned long long x = 0ull;
+        if (v < n) {
+            x = V[v];
+            if (x) V[v] = 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < kPlanes; ++i) {   // ripple-carry add of x into the planes
+            const unsigned long long c = p[i] & x;
+            p[i] ^= x;
+            x = c;
+        }
+        if ((it + 1) % 255 == 0 || it + 1 == iters) {
+            // lane l sums lane bits l and l + 32 over the warp
+            unsigned lo = 0, hi = 0;
+#pragma unroll
+            for (int i = 0; i < kPlanes; ++i) {
+                for (int j = 0; j < 32; ++j) {
+                    const unsigned cl = __popc(__ballot_sync(FULL, (p[i] >> j) & 1ull));
+                    const unsigned ch = __popc(__ballot_sync(FULL, (p[i] >> (j + 32)) & 1ull));
+                    if (lane == j) {
+                        lo += cl << i;
+                        hi += ch << i;
+                    }
+                }
+                p[i] = 0ull;
+            }
+            if (lo) atomicAdd(&s_lane[lane], lo);
+            if (hi) atomicAdd(&s_lane[lane + 32], hi);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) part_row[threadIdx.x] = s_lane[threadIdx.x];
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const uint32_t T2 = (1u << a.tile_log2) + 2u;
+    unsigned long long *s_fm = (unsigned long long *)dyn_smem;       // [T2]
+    E *s_pre = (E *)(s_fm + T2);                                     // [T2]
+    E *s_rs = s_pre + T2;                                            // [T2]
+    uint32_t *s_u = (uint32_t *)(s_rs + T2);                         // [T2]
+    uint32_t *st_w = s_u + T2;                                       // [kStage]
+    E *st_pre = (E *)(st_w + kStage);                                // [kStage]
+    E *st_d = st_pre + kStage;                                       // [kStage]
+    __shared__ Shared sh;
+    __shared__ E s_winc[kBlock], s_wpos[kBlock];
+    __shared__ unsigned long long s_acc[kBlock];
+    __shared__ unsigned s_lane[64];
+
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    unsigned long long *slots = (unsigned long long *)a.ctl->slot;
+    if (threadIdx.x == 0) {
+        sh.cnt = sh.mf = sh.stage = 0;
+        sh.limit = ~0ull;
+        sh.skipped = 0;
+        sh.qfull = 0;
+    }
+    // Launch prologue: frontier words zero.
+    for (uint64_t v = gtid; v < a.n; v += gthreads) {
+        a.F0[v] = 0ull;
+        a.F1[v] = 0ull;
+        a.F2[v] = 0ull;
+    }
+    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+    const uint64_t nb_total = *a.nbatches;
+    uint64_t rdone = 0;
+    for (uint64_t b = 0; b < nb_total; ++b) {
+        // lane table
+        if (threadIdx.x < 64) {
+            const int l = threadIdx.x;
+            const uint32_t qi = a.order[b * 64 + l];
+            sh.qi[l] = qi;
+            sh.seed[l] = qi != kEmpty ? a.seeds[qi] : 0u;
+            sh.k[l] = qi != kEmpty ? a.ks[qi] : 0u;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long acc = 0;
+            uint32_t kmax = 0;
+            for (int l = 0; l < 64; ++l) {
+                sh.deg_pre[l] = acc;
+                if (sh.qi[l] != kEmpty) {
+                    acc += (unsigned long long)(a.rp[sh.seed[l] + 1] - a.rp[sh.seed[l]]);
+                    kmax = max(kmax, sh.k[l]);
+                }
+            }
+            sh.deg_pre[64] = acc;
+            sh.kmax = kmax;
+        }
+        // seeds are visited by their own lanes
+        if (blockIdx.x == 0 && threadIdx.x < 64 && sh.qi[threadIdx.x] != kEmpty)
+            atomicOr(&a.V[sh.seed[threadIdx.x]], 1ull << threadIdx.x);
+        __syncthreads();
+        const uint32_t kmax = sh.kmax;
+        uint64_t mf = sh.deg_pre[64], items = 64, nf = 64;
+        int prev = DIR_PUSH;
+        for (uint32_t r = 1; r <= kmax && mf > 0; ++r) {
+            ++rdone;
+            const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
+            const unsigned izero = (unsigned)((rdone + 1) % 3);
+            const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
+            unsigned long long act = 0;
+            bool last = true;
+            for (int l = 0; l < 64; ++l)
+                if (sh.qi[l] != kEmpty && sh.k[l] >= r) {
+                    act |= 1ull << l;
+                    if (sh.k[l] > r) last = false;
+                }
+            int dir = DIR_PUSH;
+            if (r > 1) {
+                if (prev == DIR_PUSH) dir = ((double)mf * (double)a.alpha > (double)a.nnz) ? DIR_PULL : DIR_PUSH;
+                else dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap) ? DIR_PUSH : DIR_PULL;
+            }
+            unsigned long long *Fz = sel3(a.F0, a.F1, a.F2, izero);
+            for (uint64_t v = gtid; v < a.n; v += gthreads) Fz[v] = 0ull;
+            if (gtid == 0) {
+                slots[4 * izero + 0] = 0ull;
+                slots[4 * izero + 1] = 0ull;
+                slots[4 * izero + 3] = 0ull;
+            }
+            Round<E> R;
+            R.first = r == 1;
+            R.last = last;
+            R.act = act;
+            R.Fin = sel3(a.F0, a.F1, a.F2, iin);
+            R.Fout = sel3(a.F0, a.F1, a.F2, iout);
+            R.Q_in = qin ? a.Q1 : a.Q0;
+            R.Qpre_in = qin ? a.Qpre1 : a.Qpre0;
+            R.TF_in = qin ? a.TF1 : a.TF0;
+            R.Q_out = qout ? a.Q1 : a.Q0;
+            R.Qpre_out = qout ? a.Qpre1 : a.Qpre0;
+            R.TF_out = qout ? a.TF1 : a.TF0;
+            R.qpack_out = slots + 4 * iout;
+            R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
+            R.items_in = items;
+            R.mf = mf;
+            if (dir == DIR_PUSH)
+                push_round<E>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d);
+            else
+                pull_round<E>(a, R, sh, s_winc, s_wpos, s_acc, st_w, st_pre, st_d);
+            flush_round<E>(a, R, sh, st_w, st_pre, st_d, slots + 4 * iout);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + 4 * iout, sh.slot, 4,
+                              a.timeout_ns))
+                return;
+            nf = sh.slot[1];
+            items = sh.slot[0] >> a.ebits;
+            mf = last ? 0 : sh.slot[3];
+            prev = dir;
+        }
+        // harvest the lane counts, clear V
+        unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * 64;
+        harvest(a.V, a.n, part + (uint64_t)blockIdx.x * 64, s_lane);
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+        if (blockIdx.x == 0) {
+            // lane l is summed by the threads l, l + 64, ... over the CTAs
+            __shared__ unsigned long long s_sum[kBlock];
+            const int l = threadIdx.x & 63;
+            unsigned long long acc = 0;
+            for (uint64_t c = threadIdx.x >> 6; c < gridDim.x; c += kBlock / 64)
+                acc += part[c * 64 + l];
+            s_sum[threadIdx.x] = acc;
+            __syncthreads();
+            if (threadIdx.x < 64) {
+                unsigned long long tot = 0;
+                for (int c = 0; c < kBlock / 64; ++c) tot += s_sum[c * 64 + l];
+                if (sh.qi[l] != kEmpty) a.out[sh.qi[l]] = tot - 1ull;   // minus the seed
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Group the queries into batches of 64 by min(k, 63); answer k = 0 and
+// seeds >= n directly.  One CTA: histogram, padded exclusive scan, scatter.
+__global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, const uint32_t *ks,
+                                                     uint64_t nq, uint64_t n, uint64_t *out,
+                                                     uint32_t *order, uint64_t order_cap,
+                                                     unsigned long long *nbatches, unsigned *err) {
+    __shared__ unsigned long long cnt[kBuckets], base[kBuckets], cur[kBuckets];
+    if (threadIdx.x < kBuckets) cnt[threadIdx.x] = cur[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < nq; i += blockDim.x) {
+        const uint32_t s = seeds[i], k = ks[i];
+        if (s >= n) {
+            out[i] = ~0ull;
+            atomicOr(err, (unsigned)KHOP_DEVERR_SEED);
+        } else if (k == 0) {
+            out[i] = 0ull;
+        } else {
+            atomicAdd(&cnt[min(k, (uint32_t)kBuckets - 1)], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+            base[b] = acc;
+            acc += (cnt[b] + 63) / 64 * 64;
+        }
+        *nbatches = acc / 64;
+    }
+    __syncthreads();
+    const unsigned long long total = *nbatches * 64;
+    for (uint64_t i = threadIdx.x; i < total && i < order_cap; i += blockDim.x) order[i] = kEmpty;
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < nq; i += blockDim.x) {
+        const uint32_t s = seeds[i], k = ks[i];
+        if (s >= n || k == 0) continue;
+        const int bk = (int)min(k, (uint32_t)kBuckets - 1);
+        const unsigned long long p = base[bk] + atomicAdd(&cur[bk], 1ull);
+        if (p < order_cap) order[p] = (uint32_t)i;
+    }
+}
+
+template <typename E>
+int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
+                 uint64_t *out, cudaStream_t st) {
+    BatchState &bs = g->batch;
+    // order: nq plus up to 63 padding lanes per bucket
+    const uint64_t need = nq + 64ull * kBuckets;
+    if (bs.order_cap < need) {
+        cudaFree(bs.order);
+        bs.order = nullptr;
+        bs.order_cap = 0;
+        cudaError_t e = cudaMalloc(&bs.order, need * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_status(e);
+        bs.order_cap = need;
+    }
+    uint32_t tl = 0;
+    while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
+    const size_t T2 = (size_t(1) << tl) + 2;
+    const size_t smem = T2 * (8 + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
+    const void *fn = (const void *)batch_kernel<E>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int grid = 0;
+    int rc = cooperative_grid(fn, kBlock, smem, 0, g->num_sms, &grid);
+    if (rc != KHOP_OK) return rc;
+    if ((uint64_t)grid > bs.part_rows) return KHOP_EINVAL;
+    e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    group_kernel<<<1, 1024, 0, st>>>(seeds, ks, nq, g->n, out, bs.order, bs.order_cap,
+                                     (unsigned long long *)&bs.ctl->pad[0], &bs.ctl->err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchArgs<E> a;
+    a.n = g->n;
+    a.nnz = g->nnz;
+    a.nw = g->nw;
+    a.symmetric = g->symmetric ? 1 : 0;
+    a.rp = (const E *)g->rp;
+    a.ci = g->ci;
+    a.cp = (const E *)g->cp;
+    a.ri = g->ri;
+    a.noin = g->noin;
+    a.V = (unsigned long long *)bs.V;
+    a.F0 = (unsigned long long *)bs.F[0];
+    a.F1 = (unsigned long long *)bs.F[1];
+    a.F2 = (unsigned long long *)bs.F[2];
+    a.Q0 = bs.Q[0];
+    a.Q1 = bs.Q[1];
+    a.Qpre0 = (E *)bs.Qpre[0];
+    a.Qpre1 = (E *)bs.Qpre[1];
+    a.TF0 = bs.TF[0];
+    a.TF1 = bs.TF[1];
+    a.ctl = bs.ctl;
+    a.part = bs.part;
+    a.seeds = seeds;
+    a.ks = ks;
+    a.out = out;
+    a.order = bs.order;
+    a.nbatches = (const unsigned long long *)&bs.ctl->pad[0];
+    a.alpha = g->tune.batch_alpha;
+    a.beta = g->tune.batch_beta;
+    a.tile_log2 = tl;
+    a.ebits = g->ebits;
+    a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
+    a.pull_cap = std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.batch_beta) + 32);
+    a.timeout_ns = g->timeout_ns;
+    void *args[] = {(void *)&a};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, st);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
+                 uint64_t *out, cudaStream_t st) {
+    if (g->ewidth == 4) return launch_typed<uint32_t>(g, seeds, ks, nq, out, st);
+    return launch_typed<unsigned long long>(g, seeds, ks, nq, out, st);
 }
 
 }  // namespace khop

@@ -192,6 +192,22 @@ cudaError_t build_csc(khop_graph *g, cudaStream_t st) {
     return e != cudaSuccess ? e : e2;
 }
 
+// Bitmap of the vertices without in-edges (CSC column empty), and its count.
+template <typename E>
+__global__ void noin_kernel(const E *cp, uint64_t n, uint32_t nw, uint32_t *noin,
+                            unsigned long long *count) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw; i += stride) {
+        uint32_t w = 0;
+        for (int l = 0; l < 32; ++l) {
+            const uint64_t v = (i << 5) + l;
+            if (v < n && cp[v + 1] == cp[v]) w |= 1u << l;
+        }
+        noin[i] = w;
+        if (w) atomicAdd(count, (unsigned long long)__popc(w));
+    }
+}
+
 template <typename T>
 cudaError_t dalloc(khop_graph *g, T **p, uint64_t count) {
     const size_t bytes = std::max<uint64_t>(count, 1) * sizeof(T);
@@ -206,6 +222,10 @@ cudaError_t dalloc_raw(khop_graph *g, void **p, uint64_t bytes) {
     return e;
 }
 
+}  // namespace
+namespace khop { void free_batch_state(BatchState &b); }
+namespace {
+
 void free_graph(khop_graph *g) {
     if (!g) return;
     if (g->cp && g->cp != g->rp) cudaFree(g->cp);
@@ -213,14 +233,12 @@ void free_graph(khop_graph *g) {
     cudaFree(g->rp);
     cudaFree(g->ci);
     cudaFree(g->V);
+    cudaFree(g->V2);
+    cudaFree(g->noin);
     for (auto &f : g->F) cudaFree(f);
     for (int i = 0; i < 2; ++i) { cudaFree(g->Qpre[i]); cudaFree(g->Qrs[i]); cudaFree(g->TF[i]); }
     cudaFree(g->ctl);
-    BatchState &b = g->batch;
-    cudaFree(b.V);
-    for (int i = 0; i < 2; ++i) { cudaFree(b.F[i]); cudaFree(b.Q[i]); cudaFree(b.Qpre[i]); cudaFree(b.TF[i]); }
-    cudaFree(b.ctl);
-    cudaFree(b.lane_cnt);
+    free_batch_state(g->batch);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
 }
@@ -259,29 +277,35 @@ int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm
     return KHOP_OK;
 }
 
+void free_batch_state(BatchState &b) {
+    cudaFree(b.V);
+    for (int i = 0; i < 3; ++i) cudaFree(b.F[i]);
+    for (int i = 0; i < 2; ++i) { cudaFree(b.Q[i]); cudaFree(b.Qpre[i]); cudaFree(b.TF[i]); }
+    cudaFree(b.ctl);
+    cudaFree(b.part);
+    cudaFree(b.order);
+    b = BatchState{};
+}
+
 int ensure_batch_state(khop_graph *g) {
     BatchState &b = g->batch;
     if (b.V) return KHOP_OK;
     const uint64_t n = g->n;
     const uint64_t before = g->device_bytes;
+    b.part_rows = (uint64_t)g->num_sms * 4;
     cudaError_t e = dalloc(g, &b.V, n);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.Q[i], n);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &b.Qpre[i], n * g->ewidth);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &b.ctl, 1);
-    if (e == cudaSuccess) e = dalloc(g, &b.lane_cnt, 64);
+    if (e == cudaSuccess) e = dalloc(g, &b.part, 2 * b.part_rows * 64);
     if (e == cudaSuccess) e = cudaMemset(b.V, 0, n * sizeof(uint64_t));
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * sizeof(uint64_t));
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(CtlBlock));
-    if (e == cudaSuccess) e = cudaMemset(b.lane_cnt, 0, 64 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFree(b.V);
-        for (int i = 0; i < 2; ++i) { cudaFree(b.F[i]); cudaFree(b.Q[i]); cudaFree(b.Qpre[i]); cudaFree(b.TF[i]); }
-        cudaFree(b.ctl);
-        cudaFree(b.lane_cnt);
-        b = BatchState{};
+        free_batch_state(b);
         g->device_bytes = before;
         return cuda_status(e);
     }
@@ -411,12 +435,32 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
     g->tf_cap = nnz / 256 + 2;
     const uint64_t nw = g->nw;
     e = dalloc(g, &g->V, nw);
+    if (e == cudaSuccess) e = dalloc(g, &g->V2, nw);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &g->F[i], nw);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &g->Qpre[i], n * (uint64_t)g->ewidth);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &g->Qrs[i], n * (uint64_t)g->ewidth);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &g->TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &g->ctl, 1);
+    if (e == cudaSuccess) e = dalloc(g, &g->noin, nw);
+    if (e == cudaSuccess) {
+        unsigned long long *cnt = nullptr;
+        e = cudaMalloc(&cnt, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) {
+            if (g->ewidth == 4)
+                noin_kernel<uint32_t><<<blocks, 256, 0, st>>>((const uint32_t *)g->cp, n, g->nw, g->noin, cnt);
+            else
+                noin_kernel<unsigned long long><<<blocks, 256, 0, st>>>((const unsigned long long *)g->cp, n, g->nw, g->noin, cnt);
+            e = cudaGetLastError();
+        }
+        unsigned long long h = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        g->n_noin = h;
+        cudaFree(cnt);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(g->V, 0, nw * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->V2, 0, nw * 4, st);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(g->F[i], 0, nw * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl, 0, sizeof(CtlBlock), st);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);

@@ -67,46 +67,56 @@ __device__ __forceinline__ T warp_sum(T x) {
     return x;
 }
 
-// Words of a software grid barrier for a cooperative launch.
+// Word of a software grid barrier for a cooperative launch, alone on its
+// 128-byte line.
 struct BarrierWords {
-    unsigned count;  // CTAs arrived at the current barrier
-    unsigned gen;    // generation, bumped by the last arriver
+    unsigned count;          // sense-reversing arrival counter
+    unsigned pad[31];
 };
 
-// Grid-wide barrier over all CTAs of a cooperative launch.  Thread 0 of each
-// CTA arrives with a release and waits with an acquire, so writes made before
-// the barrier are visible to every thread after it.  The wait is bounded by
-// `timeout_ns` of %globaltimer and by an iteration cap; on expiry (or if
-// another CTA already flagged a timeout) it sets KHOP_DEVERR_TIMEOUT in *err
-// and returns false, and the caller leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, unsigned &epoch,
-                                             uint64_t timeout_ns, int *s_flag) {
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Grid-wide barrier over all CTAs of a cooperative launch: a sense-reversing
+// counter.  Every CTA adds to one 32-bit word -- CTA 0 adds 2^31 - (G - 1),
+// the other G - 1 CTAs add 1 -- so the barrier's additions total exactly 2^31:
+// the top bit flips when, and only when, the last CTA has arrived, and the low
+// bits return to where they were (no reset is ever needed).  After a CTA-wide
+// __syncthreads, thread 0 publishes the CTA's writes with a gpu-scope acq_rel
+// fence and its atomic arrival, then polls the word with acquire loads until
+// the top bit differs from the value its own atomic returned.  The wait is
+// bounded by `timeout_ns` of %globaltimer and by an iteration cap; on expiry
+// (or if another CTA already flagged a timeout) it sets KHOP_DEVERR_TIMEOUT in
+// *err and returns false, and the caller leaves the kernel.
+// If `post_n` > 0, thread 0 copies post_n 64-bit words from `post_src`
+// (global, written before the barrier) to `post_dst` (shared) after the
+// wait, so the rest of the CTA reads them from shared memory.
+__device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, int *s_flag,
+                                             const unsigned long long *post_src = nullptr,
+                                             unsigned long long *post_dst = nullptr,
+                                             int post_n = 0, uint64_t timeout_ns = 2000000000ull) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned target = epoch + 1u;
         int ok = 1;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bw->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            bw->count = 0u;
-            __threadfence();
-            st_release_u32(&bw->gen, target);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            uint64_t spins = 0;
-            while (ld_acquire_u32(&bw->gen) != target) {
-                if ((++spins & 255u) == 0u) {
-                    if (ld_volatile_u32(err) & KHOP_DEVERR_TIMEOUT) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > timeout_ns || spins > (1ull << 34)) {
-                        atomicOr(err, (unsigned)KHOP_DEVERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        fence_acq_rel_gpu();
+        const unsigned old = atomicAdd(&bw->count, add);
+        const uint64_t t0 = globaltimer_ns();
+        uint64_t spins = 0;
+        while (((ld_acquire_u32(&bw->count) ^ old) & 0x80000000u) == 0u) {
+            ++spins;
+            if ((spins & 255u) == 0u) {
+                if (ld_volatile_u32(err) & KHOP_DEVERR_TIMEOUT) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > timeout_ns || spins > (1ull << 32)) {
+                    atomicOr(err, (unsigned)KHOP_DEVERR_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        __threadfence();
-        epoch = target;
+        fence_acq_rel_gpu();
+        for (int i = 0; i < post_n; ++i) post_dst[i] = ld_relaxed_u64(post_src + i);
         *s_flag = ok;
     }
     __syncthreads();
@@ -116,30 +126,36 @@ __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, un
 // ---------------------------------------------------------------------------
 // Host side
 
-// Small device control block of a traversal state (zeroed before a launch).
+// Per-round counters of a traversal, one slot per round mod 3.
+struct RoundSlot {
+    unsigned long long qpack;     // (queue items << ebits) | out-edge prefix of the queue
+    unsigned long long nnew;      // vertices discovered
+    unsigned long long scanned;   // in-edges examined by pull
+    unsigned long long mf;        // out-edges of the vertices discovered
+};
+
+// Small device control block of a traversal state (zeroed before a launch,
+// except `err`).
 struct CtlBlock {
-    unsigned long long qpack[3];    // (queue items << ebits) | out-edge prefix, per round mod 3
-    unsigned long long nnew[3];     // vertices discovered, per round mod 3
-    unsigned long long scanned[3];  // in-edges examined by pull, per round mod 3
+    RoundSlot slot[3];
+    unsigned long long pad[4];
     BarrierWords bar;
     unsigned err;                   // sticky khop_device_error bits
-    unsigned pad;
+    unsigned pad2[31];
 };
-// Kernels address the counters as one array: qpack at [0,3), nnew at [3,6),
-// scanned at [6,9).
-static_assert(offsetof(CtlBlock, qpack) == 0 && offsetof(CtlBlock, nnew) == 24 &&
-                  offsetof(CtlBlock, scanned) == 48,
-              "CtlBlock counter layout");
 
 // Bit-sliced (64-lane) batch state of a graph.
 struct BatchState {
-    uint64_t *V = nullptr;          // visited lanes per vertex [n]
-    uint64_t *F[2] = {nullptr, nullptr};  // frontier lanes per vertex [n]
-    uint32_t *Q[2] = {nullptr, nullptr};  // union-frontier vertices with out-edges
-    void *Qpre[2] = {nullptr, nullptr};   // out-edge prefix per queue item (E)
-    uint32_t *TF[2] = {nullptr, nullptr}; // first queue item of each push tile
+    uint64_t *V = nullptr;                        // visited lanes per vertex [n]
+    uint64_t *F[3] = {nullptr, nullptr, nullptr}; // frontier lanes per vertex [n], rotating
+    uint32_t *Q[2] = {nullptr, nullptr};          // union-frontier vertices with out-edges
+    void *Qpre[2] = {nullptr, nullptr};           // out-edge prefix per queue item (E)
+    uint32_t *TF[2] = {nullptr, nullptr};         // first queue item of each push tile
     CtlBlock *ctl = nullptr;
-    unsigned long long *lane_cnt = nullptr;  // [64] per-lane counts
+    unsigned long long *part = nullptr;           // per-CTA lane counts [2][part_rows][64]
+    uint64_t part_rows = 0;
+    uint32_t *order = nullptr;                    // batch lane table (query indices)
+    uint64_t order_cap = 0;
     size_t bytes = 0;
 };
 
@@ -160,7 +176,9 @@ struct khop_graph {
     uint32_t *ri = nullptr;
 
     // plain single-query traversal state, device
-    uint32_t *V = nullptr;
+    uint32_t *V = nullptr, *V2 = nullptr;   // visited bitmaps (queries alternate)
+    uint32_t *noin = nullptr;               // bit set: vertex has no in-edge
+    uint64_t n_noin = 0;                    // vertices without in-edges
     uint32_t *F[3] = {nullptr, nullptr, nullptr};
     void *Qpre[2] = {nullptr, nullptr};
     void *Qrs[2] = {nullptr, nullptr};

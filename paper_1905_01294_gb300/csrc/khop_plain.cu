@@ -24,18 +24,23 @@ namespace {
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 
 constexpr int kPushUnroll = 4;   // edges in flight per thread in a push tile
-constexpr int kLaneScan = 4;     // in-edges a lane scans alone before the warp helps
+constexpr int kPullWords = 4;    // bitmap words a warp works on at once in a pull round
+constexpr int kFlatILP = 4;      // in-edges per lane per step of the flattened pull scan
+constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
+constexpr int kStagePosShift = 40;                       // staged count above, edges below
+constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
 
 template <typename E>
 struct PlainArgs {
-    uint64_t n, nnz;
+    uint64_t n, nnz, n_noin;
     uint32_t nw;
     int symmetric;
     const E *rp;             // CSR row offsets [n+1]
     const uint32_t *ci;      // CSR heads [nnz]
     const E *cp;             // CSC column offsets [n+1]
     const uint32_t *ri;      // CSC tails [nnz]
-    uint32_t *V;             // visited bitmap [nw]
+    const uint32_t *noin;    // vertices without in-edges [nw]
+    uint32_t *V0, *V1;       // visited bitmaps [nw]; queries alternate between them
     uint32_t *F0, *F1, *F2;  // frontier bitmaps [nw], rotating per round
     E *Qpre0, *Qpre1;        // queue: out-edge prefix per item [n], double-buffered
     E *Qrs0, *Qrs1;          // queue: row start per item [n]
@@ -54,6 +59,7 @@ struct PlainArgs {
     float alpha, beta;
     uint32_t tile_log2;
     uint32_t ebits;
+    int stage;               // stage queue items per CTA (needs nnz < 2^40)
     uint64_t pull_cap;       // queue items a pull round writes (enough for a switch back to push)
     uint64_t timeout_ns;
 };
@@ -67,6 +73,7 @@ template <typename E>
 struct Round {
     bool first, last;
     uint32_t seed;
+    uint32_t *V;             // visited bitmap of this query
     const uint32_t *Fin;
     uint32_t *Fout;
     const E *Qpre_in, *Qrs_in;
@@ -78,54 +85,142 @@ struct Round {
     uint64_t items_in, mf;   // input frontier: queue items, out-edges
 };
 
+// Per-CTA shared state of a round.
+struct Shared {
+    unsigned long long cnt;      // vertices discovered by the CTA
+    unsigned long long scan;     // in-edges the CTA examined (pull)
+    unsigned long long mf;       // out-edges of the vertices the CTA discovered
+    unsigned long long stage;    // (staged items << 40) | staged out-edges
+    unsigned long long limit;    // first staging position that did not fit (packed like stage)
+    unsigned long long gbase;    // global (items << ebits | prefix) reserved for the staged items
+    unsigned long long skipped;  // items not queued because the queue was past its cap
+    int qfull;                   // this CTA saw the queue past its cap (pull rounds)
+    unsigned long long slot[4];  // counters of the round just finished
+    int flag;
+};
+
+// Write queue item `pos` (out-edge prefix pre, row start rs, out-degree d)
+// and point every push tile that begins inside its row at it.
+template <typename E>
+__device__ __forceinline__ void put_item(const PlainArgs<E> &a, const Round<E> &R, uint64_t pos,
+                                         uint64_t pre, E rs, E d) {
+    if (pos >= R.cap) return;
+    R.Qpre_out[pos] = (E)pre;
+    R.Qrs_out[pos] = rs;
+    const uint64_t jf = (pre + (1ull << a.tile_log2) - 1ull) >> a.tile_log2;
+    const uint64_t jl = (pre + (uint64_t)d - 1ull) >> a.tile_log2;
+    for (uint64_t j = jf; j <= jl; ++j) R.TF_out[j] = (uint32_t)pos;
+}
+
 // Warp-collective bookkeeping of newly visited vertices.  `disc` marks a
-// lane's new vertex w with row start rs and out-degree d.  The count goes to
-// the CTA counter.  Unless this is the last round, vertices with out-edges
-// are appended to the next queue with their out-edge prefix (one packed
-// 64-bit atomic per warp gives both the slot and the prefix), and every push
-// tile that begins inside such a row records the row's slot.  set_f marks the
-// vertex in the next frontier bitmap (push rounds; pull rounds store whole
-// words).  Only vertices with out-edges need the bit: a pull round looks for
-// parents, and a parent has an out-edge.
+// lane's new vertex w with row start rs and out-degree d.  Counts and
+// out-edge sums go to CTA counters.  Unless this is the last round, vertices
+// with out-edges join the next queue: the warp reserves consecutive slots in
+// the CTA's shared staging area (one shared 64-bit atomic gives both the slot
+// and the out-edge prefix), and the CTA publishes the whole area with one
+// global atomic at the end of the round; a warp that finds the area full
+// appends straight to the global queue.  set_f marks the vertex in the next
+// frontier bitmap (push rounds; pull rounds store whole words).  Only vertices
+// with out-edges need the bit: a pull round looks for parents, and a parent
+// has an out-edge.
 template <typename E>
 __device__ __forceinline__ void record(const PlainArgs<E> &a, const Round<E> &R, bool disc,
-                                       uint32_t w, E rs, E d, bool set_f,
-                                       unsigned long long *s_cnt) {
+                                       uint32_t w, E rs, E d, bool set_f, Shared &sh,
+                                       E *st_pre, E *st_rs, E *st_d) {
     const unsigned m = __ballot_sync(FULL, disc);
     if (m == 0u) return;
     const int lane = threadIdx.x & 31;
-    if (lane == 0) atomicAdd(s_cnt, (unsigned long long)__popc(m));
-    if (R.last) return;
+    if (R.last) {
+        if (lane == 0) atomicAdd(&sh.cnt, (unsigned long long)__popc(m));
+        return;
+    }
     const bool has = disc && d > 0;
     if (has && set_f) atomicOr(&R.Fout[w >> 5], 1u << (w & 31));
-    const unsigned hm = __ballot_sync(FULL, has);
-    if (hm == 0u) return;
     const E dd = has ? d : (E)0;
     const E incl = warp_inclusive_sum(dd);
     const E tot = __shfl_sync(FULL, incl, 31);
+    if (lane == 0) {
+        atomicAdd(&sh.cnt, (unsigned long long)__popc(m));
+        if (tot) atomicAdd(&sh.mf, (unsigned long long)tot);
+    }
+    const unsigned hm = __ballot_sync(FULL, has);
+    if (hm == 0u) return;
     const int leader = __ffs(hm) - 1;
+    const unsigned c = __popc(hm);
+    const uint64_t rank = (uint64_t)__popc(hm & lanemask_lt());
+    const uint64_t excl = (uint64_t)(incl - dd);
     unsigned long long old = 0;
-    if (lane == leader)
-        old = atomicAdd(R.qpack_out,
-                        ((unsigned long long)__popc(hm) << a.ebits) + (unsigned long long)tot);
-    old = __shfl_sync(FULL, old, leader);
-    if (has) {
-        const uint64_t pos = (old >> a.ebits) + (uint64_t)__popc(hm & lanemask_lt());
-        const uint64_t pre = (old & ((1ull << a.ebits) - 1ull)) + (uint64_t)(incl - dd);
-        if (pos < R.cap) {
-            R.Qpre_out[pos] = (E)pre;
-            R.Qrs_out[pos] = rs;
-            const uint64_t jf = (pre + (1ull << a.tile_log2) - 1ull) >> a.tile_log2;
-            const uint64_t jl = (pre + (uint64_t)d - 1ull) >> a.tile_log2;
-            for (uint64_t j = jf; j <= jl; ++j) R.TF_out[j] = (uint32_t)pos;
+    bool staged = false;
+    if (a.stage) {
+        if (lane == leader) {
+            old = atomicAdd(&sh.stage, ((unsigned long long)c << kStagePosShift) + (unsigned long long)tot);
+            if ((old >> kStagePosShift) + c > (unsigned long long)kStage) atomicMin(&sh.limit, old);
         }
+        old = __shfl_sync(FULL, old, leader);
+        staged = (old >> kStagePosShift) + c <= (unsigned long long)kStage;
+    }
+    const int qfull = __shfl_sync(FULL, *(volatile int *)&sh.qfull, 0);   // warp-uniform
+    if (staged) {
+        if (has) {
+            const uint64_t p = (old >> kStagePosShift) + rank;
+            st_pre[p] = (E)((old & kStageEdgeMask) + excl);
+            st_rs[p] = rs;
+            st_d[p] = d;
+        }
+    } else if (qfull) {
+        // A pull round whose queue is already past its cap: the next round
+        // pulls too, so only the item count is kept.
+        if (lane == leader) atomicAdd(&sh.skipped, (unsigned long long)c);
+    } else {
+        if (lane == leader) {
+            old = atomicAdd(R.qpack_out, ((unsigned long long)c << a.ebits) + (unsigned long long)tot);
+            if ((old >> a.ebits) + c > R.cap) sh.qfull = 1;
+        }
+        old = __shfl_sync(FULL, old, leader);
+        if (has)
+            put_item(a, R, (old >> a.ebits) + rank, (old & ((1ull << a.ebits) - 1ull)) + excl, rs, d);
+    }
+}
+
+// End of a round for one CTA: publish the staged queue items and flush the
+// CTA counters.  Called by all threads of the CTA.
+template <typename E, int BLOCK>
+__device__ __forceinline__ void flush_round(const PlainArgs<E> &a, const Round<E> &R, Shared &sh,
+                                            E *st_pre, E *st_rs, E *st_d,
+                                            unsigned long long *slot_out) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long st = sh.stage;
+        if (sh.limit < st) st = sh.limit;   // staged items are the prefix before the first miss
+        const uint32_t nst = (uint32_t)(st >> kStagePosShift);
+        if (nst)
+            sh.gbase = atomicAdd(R.qpack_out, ((unsigned long long)nst << a.ebits) +
+                                                  (st & kStageEdgeMask));
+        if (sh.skipped) atomicAdd(R.qpack_out, sh.skipped << a.ebits);
+        sh.skipped = 0;
+        sh.qfull = 0;
+        if (sh.cnt) atomicAdd(slot_out + 1, sh.cnt);
+        if (sh.scan) atomicAdd(slot_out + 2, sh.scan);
+        if (sh.mf) atomicAdd(slot_out + 3, sh.mf);
+        sh.cnt = sh.scan = sh.mf = 0;
+        sh.stage = 0;
+        sh.limit = ~0ull;
+        sh.flag = (int)nst;
+    }
+    __syncthreads();
+    const uint32_t nst = (uint32_t)sh.flag;
+    if (nst) {
+        const uint64_t gpos = sh.gbase >> a.ebits;
+        const uint64_t gpre = sh.gbase & ((1ull << a.ebits) - 1ull);
+        for (uint32_t t = threadIdx.x; t < nst; t += BLOCK)
+            put_item(a, R, gpos + t, gpre + (uint64_t)st_pre[t], st_rs[t], st_d[t]);
     }
 }
 
 // Push round: tiles of T consecutive frontier out-edges, one CTA per tile.
 template <typename E, int BLOCK>
-__device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E> &R, E *s_pre, E *s_rs,
-                           unsigned long long *s_cnt) {
+__device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E> &R, E *s_pre,
+                                           E *s_rs, Shared &sh, E *st_pre, E *st_rs, E *st_d) {
     const uint32_t tl = a.tile_log2;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
@@ -173,102 +268,156 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
                 bool disc = false;
                 if (ok[u]) {
                     const uint32_t wi = w[u] >> 5, bit = 1u << (w[u] & 31);
-                    if (!(a.V[wi] & bit)) disc = !(atomicOr(&a.V[wi], bit) & bit);
+                    if (!(R.V[wi] & bit)) disc = !(atomicOr(&R.V[wi], bit) & bit);
                 }
                 E rs = 0, d = 0;
                 if (disc && !R.last) {
                     rs = a.rp[w[u]];
                     d = a.rp[w[u] + 1] - rs;
                 }
-                record(a, R, disc, w[u], rs, d, true, s_cnt);
+                record(a, R, disc, w[u], rs, d, true, sh, st_pre, st_rs, st_d);
             }
         }
         __syncthreads();
     }
 }
 
-// Pull round: one warp per 32-vertex bitmap word; each unvisited vertex looks
-// for an in-neighbour in the frontier bitmap and stops at the first.
+// Pull round (masked SpMV over the unvisited vertices).  A warp takes
+// kPullWords 32-vertex bitmap words at once (lane l owns vertex 32 i + l of
+// each), so their loads are in flight together.  Every unvisited vertex first
+// checks its first two in-edges against the frontier bitmap; the in-edges of
+// the vertices still unresolved are then scanned word by word as one
+// flattened list: the warp takes the next 32 * kFlatILP edges of the
+// concatenated remaining in-edge lists (a load-balanced search over the
+// lanes' remaining counts), and a vertex drops out as soon as one of its
+// in-neighbours is in the frontier.
 template <typename E, int BLOCK>
-__device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E> &R, unsigned long long *s_cnt,
-                           unsigned long long *s_scan) {
+__device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E> &R, Shared &sh,
+                                           E *s_winc, E *s_wpos, E *st_pre, E *st_rs, E *st_d) {
     const int lane = threadIdx.x & 31;
+    E *winc = s_winc + (threadIdx.x >> 5) * 32;
+    E *wpos = s_wpos + (threadIdx.x >> 5) * 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * BLOCK) >> 5;
     uint64_t scanned = 0;
-    for (uint64_t i = gwarp; i < a.nw; i += nwarps) {
-        const uint32_t Vw = a.V[i];
-        const uint64_t v = (i << 5) + (uint64_t)lane;
-        const bool unv = v < a.n && !((Vw >> lane) & 1u);
-        if (__ballot_sync(FULL, unv) == 0u) {
-            if (lane == 0) R.Fout[i] = 0u;
-            continue;
+    for (uint64_t i0 = gwarp * kPullWords; i0 < a.nw; i0 += nwarps * kPullWords) {
+        uint32_t Vw[kPullWords];
+        bool unv[kPullWords], found[kPullWords];
+        E b[kPullWords], e[kPullWords], pos[kPullWords];
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            const uint64_t i = i0 + j;
+            Vw[j] = i < a.nw ? R.V[i] : ~0u;
+            const uint64_t v = (i << 5) + (uint64_t)lane;
+            unv[j] = i < a.nw && v < a.n && !((Vw[j] >> lane) & 1u);
+            found[j] = false;
         }
-        E b = 0, e = 0;
-        if (unv) {
-            b = a.cp[v];
-            e = a.cp[v + 1];
-        }
-        bool found = false;
-        E pos = b;
-        for (int t = 0; t < kLaneScan; t += 2) {
-            const bool l0 = unv && !found && pos < e;
-            const bool l1 = l0 && pos + 1 < e;
-            uint32_t u0 = 0, u1 = 0;
-            if (l0) u0 = a.ri[pos];
-            if (l1) u1 = a.ri[pos + 1];
-            bool h = false;
-            if (l0) h = (R.Fin[u0 >> 5] >> (u0 & 31)) & 1u;
-            if (l1) h = h || ((R.Fin[u1 >> 5] >> (u1 & 31)) & 1u);
-            scanned += (uint64_t)l0 + (uint64_t)l1;
-            pos += (E)l0 + (E)l1;
-            found = found || h;
-            if (!__any_sync(FULL, unv && !found && pos < e)) break;
-        }
-        unsigned rem = __ballot_sync(FULL, unv && !found && pos < e);
-        while (rem) {
-            const int L = __ffs(rem) - 1;
-            const E lb = __shfl_sync(FULL, pos, L), le = __shfl_sync(FULL, e, L);
-            bool hit = false;
-            for (E c = lb; c < le; c += 32) {
-                const E idx = c + (E)lane;
-                bool h = false;
-                if (idx < le) {
-                    const uint32_t u = a.ri[idx];
-                    h = (R.Fin[u >> 5] >> (u & 31)) & 1u;
-                    ++scanned;
-                }
-                if (__any_sync(FULL, h)) { hit = true; break; }
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            b[j] = 0;
+            e[j] = 0;
+            if (unv[j]) {
+                const uint64_t v = ((i0 + j) << 5) + (uint64_t)lane;
+                b[j] = a.cp[v];
+                e[j] = a.cp[v + 1];
             }
-            if (lane == L) found = hit;
-            rem &= rem - 1u;
+            pos[j] = b[j];
         }
-        const unsigned nm = __ballot_sync(FULL, found);
-        if (lane == 0) {
-            R.Fout[i] = nm;
-            if (nm) a.V[i] = Vw | nm;
+        uint32_t u0[kPullWords], u1[kPullWords];
+        bool l0[kPullWords], l1[kPullWords];
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            l0[j] = unv[j] && pos[j] < e[j];
+            l1[j] = l0[j] && pos[j] + 1 < e[j];
+            u0[j] = l0[j] ? a.ri[pos[j]] : 0u;
+            u1[j] = l1[j] ? a.ri[pos[j] + 1] : 0u;
         }
-        E rs = 0, d = 0;
-        if (found && !R.last) {
-            if (a.symmetric) { rs = b; d = e - b; }
-            else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            bool h = l0[j] && ((R.Fin[u0[j] >> 5] >> (u0[j] & 31)) & 1u);
+            h = h || (l1[j] && ((R.Fin[u1[j] >> 5] >> (u1[j] & 31)) & 1u));
+            found[j] = h;
+            pos[j] += (E)l0[j] + (E)l1[j];
+            scanned += (uint64_t)l0[j] + (uint64_t)l1[j];
         }
-        record(a, R, found, (uint32_t)v, rs, d, false, s_cnt);
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            E rem = (unv[j] && !found[j]) ? e[j] - pos[j] : (E)0;
+            while (__any_sync(FULL, rem > 0)) {
+                const E incl = warp_inclusive_sum(rem);
+                const E total = __shfl_sync(FULL, incl, 31);
+                const E excl = incl - rem;
+                winc[lane] = incl;
+                wpos[lane] = pos[j] - excl;   // edge of flat index x owned by lane L: wpos[L] + x
+                __syncwarp();
+                const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
+                uint32_t uu[kFlatILP];
+                int own[kFlatILP];
+#pragma unroll
+                for (int t = 0; t < kFlatILP; ++t) {
+                    const uint32_t x = (uint32_t)(t * 32 + lane);
+                    own[t] = -1;
+                    uu[t] = 0;
+                    if (x < chunk) {
+                        int lo = 0, hi = 31;   // first lane whose inclusive count exceeds x
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
+                        }
+                        own[t] = lo;
+                        uu[t] = a.ri[wpos[lo] + (E)x];
+                    }
+                }
+                unsigned hits = 0;
+#pragma unroll
+                for (int t = 0; t < kFlatILP; ++t)
+                    if (own[t] >= 0 && ((R.Fin[uu[t] >> 5] >> (uu[t] & 31)) & 1u))
+                        hits |= 1u << own[t];
+                hits = __reduce_or_sync(FULL, hits);
+                const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
+                pos[j] += consumed;
+                rem -= consumed;
+                if ((hits >> lane) & 1u) {
+                    found[j] = true;
+                    rem = 0;
+                }
+                if (lane == 0) scanned += chunk;
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPullWords; ++j) {
+            const uint64_t i = i0 + j;
+            if (i >= a.nw) break;
+            const unsigned nm = __ballot_sync(FULL, found[j]);
+            if (lane == 0) {
+                R.Fout[i] = nm;
+                if (nm) R.V[i] = Vw[j] | nm;
+            }
+            const uint64_t v = (i << 5) + (uint64_t)lane;
+            E rs = 0, d = 0;
+            if (found[j] && !R.last) {
+                if (a.symmetric) { rs = b[j]; d = e[j] - b[j]; }
+                else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
+            }
+            record(a, R, found[j], (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
+        }
     }
     scanned = warp_sum(scanned);
-    if (lane == 0 && scanned) atomicAdd(s_scan, (unsigned long long)scanned);
+    if (lane == 0 && scanned) atomicAdd(&sh.scan, (unsigned long long)scanned);
 }
 
-// Answer queries that need no traversal (k = 0, or a seed >= n) and return
-// the index of the next query that does.  Only thread 0 of CTA 0 writes.
+// Answer the queries that need no traversal -- k = 0, a seed >= n, or a seed
+// without out-edges (count 0 and TE 0) -- and return the index of the next
+// query that does.  Only thread 0 of CTA 0 writes (when `write` is set).
 template <typename E>
-__device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t q, bool b0,
+__device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t q, bool write,
                                                  uint64_t &t_prev) {
     for (; q < a.nq; ++q) {
         const uint32_t s = a.seeds[q];
         const uint32_t k = a.ks ? a.ks[q] : a.k_all;
-        if (s < a.n && k > 0) break;
-        if (b0) {
+        if (s < a.n && k > 0 && a.rp[s + 1] > a.rp[s]) break;
+        if (write) {
             const bool bad = s >= a.n;
             const uint64_t now = globaltimer_ns();
             a.out[q] = bad ? ~0ull : 0ull;
@@ -287,11 +436,12 @@ __device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t
     return q;
 }
 
-// Zero V and the frontier bitmaps, then set the seed of query q in V and in
-// the bitmap that round 1 reads (rdone = rounds run so far in the launch).
+// Visited bitmap for the next query: the vertices without in-edges (no round
+// can reach them, so marking them spares the pull sweeps) plus the seed of
+// query q.  Grid-stride over the words.
 template <typename E>
-__device__ __forceinline__ void clean_prep(const PlainArgs<E> &a, uint64_t q, uint64_t rdone,
-                                           uint64_t gtid, uint64_t gthreads) {
+__device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V, uint64_t q,
+                                             uint64_t gtid, uint64_t gthreads) {
     uint64_t sw = ~0ull;
     uint32_t sb = 0;
     if (q < a.nq) {
@@ -299,48 +449,63 @@ __device__ __forceinline__ void clean_prep(const PlainArgs<E> &a, uint64_t q, ui
         sw = s >> 5;
         sb = 1u << (s & 31);
     }
-    const unsigned fin = (unsigned)(rdone % 3);
-    for (uint64_t i = gtid; i < a.nw; i += gthreads) {
-        const uint32_t val = i == sw ? sb : 0u;
-        a.V[i] = val;
-        a.F0[i] = fin == 0 ? val : 0u;
-        a.F1[i] = fin == 1 ? val : 0u;
-        a.F2[i] = fin == 2 ? val : 0u;
-    }
+    for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = a.noin[i] | (i == sw ? sb : 0u);
 }
 
 template <typename E, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) plain_kernel(const PlainArgs<E> a) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainArgs<E> a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    E *s_pre = (E *)dyn_smem;
+    E *s_pre = (E *)dyn_smem;                         // push tile items [T + 2]
     E *s_rs = s_pre + ((1u << a.tile_log2) + 2u);
-    __shared__ unsigned long long s_cnt, s_scan;
-    __shared__ int s_flag;
+    E *st_pre = s_rs + ((1u << a.tile_log2) + 2u);    // staged queue items [kStage]
+    E *st_rs = st_pre + kStage;
+    E *st_d = st_rs + kStage;
+    __shared__ Shared sh;
+    __shared__ E s_winc[BLOCK], s_wpos[BLOCK];        // flattened pull scan, 32 per warp
 
     const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
     const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * BLOCK;
-    unsigned epoch = 0;
     if (threadIdx.x == 0) {
-        s_cnt = 0;
-        s_scan = 0;
-        epoch = ld_volatile_u32(&a.ctl->bar.gen);
+        sh.cnt = sh.scan = sh.mf = sh.stage = 0;
+        sh.limit = ~0ull;
+        sh.skipped = 0;
+        sh.qfull = 0;
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
     __syncthreads();
 
-    const uint64_t emask = (1ull << a.ebits) - 1ull;
+    const bool all_pull = a.direction == KHOP_DIR_PULL;
+    unsigned long long *slots = (unsigned long long *)a.ctl->slot;
+
+    // Launch prologue: frontier bitmaps zero, V0 = noin | {first seed}.
+    uint64_t q = skip_trivial(a, 0, b0, t_prev);
+    for (uint64_t i = gtid; i < a.nw; i += gthreads) {
+        a.F0[i] = 0u;
+        a.F1[i] = 0u;
+        a.F2[i] = 0u;
+    }
+    prep_visited(a, a.V0, q, gtid, gthreads);
+    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
 
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
-    uint64_t q = skip_trivial(a, 0, b0, t_prev);
-    clean_prep(a, q, rdone, gtid, gthreads);
-    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, epoch, a.timeout_ns, &s_flag)) return;
-
+    unsigned par = 0;     // which visited bitmap the current query uses
     while (q < a.nq) {
         const uint32_t s = a.seeds[q];
         const uint32_t k = a.ks ? a.ks[q] : a.k_all;
+        uint32_t *V = par ? a.V1 : a.V0;
+        uint32_t *Vnext = par ? a.V0 : a.V1;
+        const uint64_t qn = skip_trivial(a, q + 1, false, t_prev);   // next query (no writes)
+        if (all_pull) {
+            // Round 1 pulls from the bitmap {s}: set it up before the round.
+            uint32_t *Fs = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
+            const uint64_t sw = s >> 5;
+            for (uint64_t i = gtid; i < a.nw; i += gthreads) Fs[i] = i == sw ? 1u << (s & 31) : 0u;
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns))
+                return;
+        }
         uint64_t mf = (uint64_t)(a.rp[s + 1] - a.rp[s]);   // out-edges of the frontier {s}
-        uint64_t items = mf > 0 ? 1 : 0;
+        uint64_t items = 1;
         uint64_t nf = 1;
         uint64_t count = 0, te = 0, bytes = 0, sum_mf = 0, visited = 1;
         uint32_t rounds = 0, pull_mask = 0;
@@ -351,9 +516,9 @@ __global__ void __launch_bounds__(BLOCK) plain_kernel(const PlainArgs<E> a) {
             const unsigned izero = (unsigned)((rdone + 1) % 3);
             const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
             int dir;
-            if (r == 1) dir = a.direction == KHOP_DIR_PULL ? DIR_PULL : DIR_PUSH;
+            if (r == 1) dir = all_pull ? DIR_PULL : DIR_PUSH;
             else if (a.direction == KHOP_DIR_PUSH) dir = DIR_PUSH;
-            else if (a.direction == KHOP_DIR_PULL) dir = DIR_PULL;
+            else if (all_pull) dir = DIR_PULL;
             else {
                 const uint64_t mu = a.nnz - (sum_mf + mf);   // out-edges of unvisited vertices
                 if (prev == DIR_PUSH)
@@ -362,20 +527,23 @@ __global__ void __launch_bounds__(BLOCK) plain_kernel(const PlainArgs<E> a) {
                     dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap)
                               ? DIR_PUSH : DIR_PULL;
             }
-            // Zero what round r+1 will write (read last in round r-1).
+            // Zero what round r+1 writes (last read in round r-1); in round 1
+            // also prepare the next query's visited bitmap.
             uint32_t *Fz = sel3(a.F0, a.F1, a.F2, izero);
             for (uint64_t i = gtid; i < a.nw; i += gthreads) Fz[i] = 0u;
+            if (r == 1) prep_visited(a, Vnext, qn, gtid, gthreads);
             if (b0) {
-                unsigned long long *c = (unsigned long long *)a.ctl;
-                c[izero] = 0ull;        // qpack
-                c[3 + izero] = 0ull;    // nnew
-                c[6 + izero] = 0ull;    // scanned
+                slots[4 * izero + 0] = 0ull;
+                slots[4 * izero + 1] = 0ull;
+                slots[4 * izero + 2] = 0ull;
+                slots[4 * izero + 3] = 0ull;
             }
             te += mf;
             Round<E> R;
             R.first = r == 1;
             R.last = r == k;
             R.seed = s;
+            R.V = V;
             R.Fin = sel3(a.F0, a.F1, a.F2, iin);
             R.Fout = sel3(a.F0, a.F1, a.F2, iout);
             R.Qpre_in = qin ? a.Qpre1 : a.Qpre0;
@@ -384,41 +552,39 @@ __global__ void __launch_bounds__(BLOCK) plain_kernel(const PlainArgs<E> a) {
             R.Qpre_out = qout ? a.Qpre1 : a.Qpre0;
             R.Qrs_out = qout ? a.Qrs1 : a.Qrs0;
             R.TF_out = qout ? a.TF1 : a.TF0;
-            R.qpack_out = (unsigned long long *)a.ctl + iout;
+            R.qpack_out = slots + 4 * iout;
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
             R.items_in = items;
             R.mf = mf;
-            if (dir == DIR_PUSH) push_round<E, BLOCK>(a, R, s_pre, s_rs, &s_cnt);
-            else pull_round<E, BLOCK>(a, R, &s_cnt, &s_scan);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (s_cnt) atomicAdd((unsigned long long *)a.ctl + 3 + iout, s_cnt);
-                if (s_scan) atomicAdd((unsigned long long *)a.ctl + 6 + iout, s_scan);
-                s_cnt = 0;
-                s_scan = 0;
-            }
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, epoch, a.timeout_ns, &s_flag)) return;
-            const unsigned long long qp = ld_relaxed_u64((unsigned long long *)a.ctl + iout);
-            const uint64_t nnew = ld_relaxed_u64((unsigned long long *)a.ctl + 3 + iout);
-            const uint64_t scn = ld_relaxed_u64((unsigned long long *)a.ctl + 6 + iout);
+            if (dir == DIR_PUSH) push_round<E, BLOCK>(a, R, s_pre, s_rs, sh, st_pre, st_rs, st_d);
+            else pull_round<E, BLOCK>(a, R, sh, s_winc, s_wpos, st_pre, st_rs, st_d);
+            flush_round<E, BLOCK>(a, R, sh, st_pre, st_rs, st_d, slots + 4 * iout);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + 4 * iout, sh.slot, 4,
+                              a.timeout_ns))
+                return;
+            const unsigned long long qp = sh.slot[0];
+            const uint64_t nnew = sh.slot[1];
+            const uint64_t scn = sh.slot[2];
             const uint64_t W = sizeof(E);
             const uint64_t items_out = R.last ? 0 : min((uint64_t)(qp >> a.ebits), R.cap);
-            if (dir == DIR_PUSH)
+            if (dir == DIR_PUSH) {
                 bytes += 4ull * mf + 2ull * W * ((r == 1 ? 1ull : items) + items_out);
-            else
-                bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * (a.n - visited) + 4ull * scn +
+            } else {
+                const uint64_t seen = visited + a.n_noin;
+                const uint64_t unvisited = a.n > seen ? a.n - seen : 0;
+                bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn +
                          2ull * W * items_out;
+            }
             sum_mf += mf;
             count += nnew;
             visited += nnew;
             nf = nnew;
             items = qp >> a.ebits;
-            mf = R.last ? 0 : (qp & emask);
+            mf = R.last ? 0 : sh.slot[3];
             prev = dir;
             rounds = r;
             if (dir == DIR_PULL && r <= 32) pull_mask |= 1u << (r - 1);
             if (b0 && a.per_hop && r < a.hop_stride) a.per_hop[q * a.hop_stride + r] = nnew;
-            (void)nf;
         }
         if (b0) {
             const uint64_t now = globaltimer_ns();
@@ -434,11 +600,10 @@ __global__ void __launch_bounds__(BLOCK) plain_kernel(const PlainArgs<E> a) {
                     a.per_hop[q * a.hop_stride + r] = 0ull;
             }
             t_prev = now;
+            skip_trivial(a, q + 1, true, t_prev);   // answer the trivial queries up to qn
         }
-        const uint64_t qn = skip_trivial(a, q + 1, b0, t_prev);
-        clean_prep(a, qn, rdone, gtid, gthreads);
-        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, epoch, a.timeout_ns, &s_flag)) return;
         q = qn;
+        par ^= 1u;
     }
 }
 
@@ -450,7 +615,7 @@ int launch_block(khop_graph *g, PlainArgs<E> &a, size_t smem, cudaStream_t st) {
     int grid = 0;
     int rc = cooperative_grid(fn, BLOCK, smem, g->tune.blocks_per_sm, g->num_sms, &grid);
     if (rc != KHOP_OK) return rc;
-    e = cudaMemsetAsync(g->ctl, 0, offsetof(CtlBlock, err), st);
+    e = cudaMemsetAsync(g->ctl, 0, offsetof(CtlBlock, err), st);   // keeps the sticky err
     if (e != cudaSuccess) return cuda_status(e);
     void *args[] = {(void *)&a};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, smem, st);
@@ -464,13 +629,16 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
     PlainArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
+    a.n_noin = g->n_noin;
     a.nw = g->nw;
     a.symmetric = g->symmetric ? 1 : 0;
     a.rp = (const E *)g->rp;
     a.ci = g->ci;
     a.cp = (const E *)g->cp;
     a.ri = g->ri;
-    a.V = g->V;
+    a.noin = g->noin;
+    a.V0 = g->V;
+    a.V1 = g->V2;
     a.F0 = g->F[0];
     a.F1 = g->F[1];
     a.F2 = g->F[2];
@@ -497,11 +665,12 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
     while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
     a.tile_log2 = tl;
     a.ebits = g->ebits;
+    a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
     a.pull_cap = g->tune.direction == KHOP_DIR_PULL
                      ? 0ull
                      : std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.beta) + 32);
     a.timeout_ns = g->timeout_ns;
-    const size_t smem = 2 * ((size_t(1) << tl) + 2) * sizeof(E);
+    const size_t smem = (2 * ((size_t(1) << tl) + 2) + 3 * (size_t)kStage) * sizeof(E);
     switch (g->tune.block_threads) {
         case 256: return launch_block<E, 256>(g, a, smem, st);
         case 1024: return launch_block<E, 1024>(g, a, smem, st);

@@ -327,7 +327,7 @@ class Graph:
             if not x.is_cuda or x.dtype not in (torch.int32, torch.uint32):
                 raise TypeError("expected a CUDA int32/uint32 tensor")
             return x.contiguous()
-        a = np.ascontiguousarray(np.asarray(x, dtype=np.uint32))
+        a = np.array(x, dtype=np.uint32, copy=True).reshape(-1)
         return torch.from_numpy(a.view(np.int32)).cuda()
 
     def count(self, seeds, k, stream=None):

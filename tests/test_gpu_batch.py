@@ -1,0 +1,133 @@
+"""GPU parity of the 64-lane bit-sliced batched path.
+
+Each lane's count must equal the oracle's (and the plain path's) exactly,
+whatever the lane, the batch and the mix of k around it: the batched counts
+are compared with the oracle on the same seeded inputs, and with themselves
+under a permutation of the query order.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+kh = pytest.importorskip("paper_1905_01294_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+    kh.lib()
+
+
+def batched(G, seeds, ks):
+    out = G.count_mixed(np.asarray(seeds, np.uint32), np.asarray(ks, np.uint32),
+                        mode=kh.MODE_BATCHED64)
+    torch.cuda.synchronize()
+    return kh.as_u64(out)
+
+
+def check(g, seeds, ks, wide=False, **tune):
+    G = kh.Graph.from_csr(g, wide=wide)
+    if tune:
+        G.set_tuning(**tune)
+    seeds = np.asarray(seeds, np.uint32)
+    ks = np.broadcast_to(np.asarray(ks, np.uint32), seeds.shape).copy()
+    want, _ = oracle.khop_counts(g, seeds, np.minimum(ks, g.n + 1))
+    got = batched(G, seeds, ks)
+    np.testing.assert_array_equal(got, want)
+    # lane/batch invariance: a permuted query order gives the same per-query counts
+    perm = np.random.default_rng(len(seeds)).permutation(len(seeds))
+    got_p = batched(G, seeds[perm], ks[perm])
+    np.testing.assert_array_equal(got_p, want[perm])
+    bits = G.error_bits()
+    G.close()
+    return bits
+
+
+def test_rmat_scale10_mixed_k():
+    g = gen.rmat(10, 16, seed=1)
+    seeds = gen.seeds(g, 64, seed=2)
+    ks = np.tile(np.array([1, 2, 3, 6], np.uint32), 16)
+    assert check(g, seeds, ks) == 0
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 6])
+def test_rmat_scale10_every_vertex(k):
+    g = gen.rmat(10, 16, seed=1)
+    assert check(g, np.arange(g.n, dtype=np.uint32), k) == 0
+
+
+def test_symmetric_scale12_many_batches_wide():
+    g = gen.rmat(12, 16, seed=3, symmetrize=True)
+    seeds = gen.seeds(g, 700, seed=4)
+    ks = gen.mixed_ks(700, seed=5)
+    assert check(g, seeds, ks, wide=True) == 0
+
+
+@pytest.mark.parametrize("alpha,beta,tile", [(1e-6, 1e6, 256), (1e6, 1e-6, 8192), (14, 24, 1024)])
+def test_direction_extremes(alpha, beta, tile):
+    """alpha tiny: pull from round 2 on; alpha huge: push only."""
+    g = gen.rmat(11, 16, seed=6)
+    seeds = gen.seeds(g, 200, seed=7)
+    ks = gen.mixed_ks(200, choices=(1, 2, 3, 4, 6), seed=8)
+    assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=beta, push_tile=tile) == 0
+
+
+def test_edge_cases_k0_bad_seed_duplicates_and_sinks():
+    g = gen.csr_raw(40, [0, 0, 1, 2, 3, 3, 5, 5, 7], [1, 1, 2, 3, 0, 3, 5, 6, 7])
+    seeds = np.array([0, 0, 0, 3, 39, 5, 7, 40, 1000, 2, 6, 1], np.uint32)
+    ks = np.array([1, 2, 0, 6, 3, 2, 4, 2, 1, 2**31, 3, 5], np.uint32)
+    G = kh.Graph.from_csr(g)
+    got = batched(G, seeds, ks)
+    ok = seeds < g.n
+    want, _ = oracle.khop_counts(g, seeds[ok], np.minimum(ks[ok], 100))
+    np.testing.assert_array_equal(got[ok], want)
+    assert (got[~ok] == np.uint64(2**64 - 1)).all()
+    assert G.error_bits() & kh.DEVERR_SEED
+    G.close()
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 100])
+def test_small_named_graphs(n):
+    for g in (gen.path_graph(n), gen.cycle_graph(n), gen.complete_graph(min(n, 40)),
+              gen.empty_graph(n), gen.sym_star(n)):
+        seeds = np.arange(g.n, dtype=np.uint32)
+        ks = (np.arange(g.n) % 7).astype(np.uint32)
+        assert check(g, seeds, ks) == 0
+
+
+def test_random_multigraphs():
+    rng = np.random.default_rng(77)
+    for _ in range(8):
+        n = int(rng.integers(1, 400))
+        m = int(rng.integers(0, 8 * n + 1))
+        g = gen.csr_raw(n, rng.integers(0, n, m), rng.integers(0, n, m))
+        nq = int(rng.integers(1, 200))
+        seeds = rng.integers(0, n, nq).astype(np.uint32)
+        ks = rng.choice([0, 1, 2, 3, 6, 9], nq).astype(np.uint32)
+        assert check(g, seeds, ks) == 0
+
+
+def test_batched_equals_plain_on_scale21_mixed_workload():
+    """4096 seeds with k uniform over {1,2,3,6} on the scale-21 symmetrized
+    Kronecker graph: every batched count equals the plain path's count, and a
+    sample of 256 equals the oracle's."""
+    g = gen.rmat(21, 16, seed=1, symmetrize=True)
+    G = kh.Graph.from_csr(g)
+    seeds = gen.seeds(g, 4096, seed=2)
+    ks = gen.mixed_ks(4096, seed=2)
+    got = batched(G, seeds, ks)
+    plain = G.count_mixed(seeds, ks, mode=kh.MODE_PLAIN)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got, kh.as_u64(plain))
+    idx = np.random.default_rng(3).choice(4096, 256, replace=False)
+    want, _ = oracle.khop_counts(g, seeds[idx], ks[idx])
+    np.testing.assert_array_equal(got[idx], want)
+    assert G.error_bits() == 0
+    G.close()
