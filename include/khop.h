@@ -190,6 +190,39 @@ int khop_count_ex(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint
                   uint64_t *out_counts, uint64_t *out_te, khop_query_stats *out_stats,
                   uint64_t *per_hop, uint32_t hop_stride, void *stream);
 
+/*
+ * khop_count without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * whose device memory is owned by another allocator (for example a
+ * framework's caching pool that has reserved the GPU), and latency-critical
+ * callers that cannot afford the implicit device synchronisation of an
+ * allocation.  Such callers cannot create a khop_graph either, so they pass
+ * the graph itself as device arrays.
+ *   n            vertices, 1 <= n <= 2^20 (1,048,576)
+ *   row_ptr      device uint32[n+1]: CSR row offsets (out-edges)
+ *   col_idx      device uint32[nnz]: CSR heads
+ *   col_ptr      device uint32[n+1] or NULL: CSC column offsets (in-edges)
+ *   row_idx      device uint32[nnz] or NULL: CSC tails (NULL exactly when
+ *                col_ptr is); with a CSC the traversal switches between push
+ *                and pull, without one it only pushes.  Passing the CSR
+ *                arrays again declares the graph symmetric.
+ *   nnz          edges, <= 2^26 (67,108,864)
+ *   seeds, nseeds, k, out_counts, stream: as for khop_count
+ * The traversal state lives in one fixed device array of about 20 MB that
+ * every GPU which loads this library holds until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and the next call overwrites it, so calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race: order them on one stream.  Each call resets the state it needs.
+ * Errors: EINVAL for sizes beyond the limits or bad pointers, ECUDA.  A seed
+ * >= n gives UINT64_MAX (no sticky error word is kept).
+ */
+int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint32_t *col_idx,
+                      const uint32_t *col_ptr, const uint32_t *row_idx, uint64_t nnz,
+                      const uint32_t *seeds, uint64_t nseeds, uint32_t k,
+                      uint64_t *out_counts, void *stream);
+
 /* Read and clear the graph's sticky device error bits (synchronises the device). */
 int khop_get_error(khop_graph *g, uint32_t *device_error_bits);
 

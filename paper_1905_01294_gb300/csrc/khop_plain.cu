@@ -691,3 +691,155 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
 }
 
 }  // namespace khop
+
+// ===========================================================================
+// Allocation-free variant of the plain count (khop_count_static).
+//
+// Its traversal state lives in one file-scope device array of fixed size,
+// so the entry point never allocates device memory.  Every GPU that loads
+// the library holds the array until the process exits.  Host code reaches
+// it only through the address cudaGetSymbolAddress returns for the current
+// device (the array's name in host code is a host-side stand-in, not a
+// device address).
+
+namespace khop {
+namespace {
+
+constexpr uint64_t kStaticMaxN = 1ull << 20;      // vertices
+constexpr uint64_t kStaticMaxNnz = 1ull << 26;    // edges
+constexpr uint64_t kStaticNw = kStaticMaxN / 32;
+constexpr uint64_t kStaticTF = kStaticMaxNnz / 256 + 2;   // push tiles of >= 256 edges
+constexpr uint64_t kWordsPer256 = 64;
+constexpr uint64_t round64(uint64_t x) { return (x + kWordsPer256 - 1) / kWordsPer256 * kWordsPer256; }
+// layout in 32-bit words, every part 256-byte aligned
+constexpr uint64_t kOffCtl = 0;
+constexpr uint64_t kOffBits = round64(sizeof(CtlBlock) / 4);         // V0 V1 F0 F1 F2 noin
+constexpr uint64_t kOffQ = kOffBits + 6 * round64(kStaticNw);        // Qpre0 Qpre1 Qrs0 Qrs1
+constexpr uint64_t kOffTF = kOffQ + 4 * round64(kStaticMaxN);        // TF0 TF1
+constexpr uint64_t kStaticWords = kOffTF + 2 * round64(kStaticTF);
+
+static __device__ __align__(256) uint32_t g_static_scratch[kStaticWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint32_t *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up once
+// per device, with that device current).
+int static_scratch(uint32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kMaxDevices) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_static_ptr[dev] = (uint32_t *)p;
+    }
+    *out = g_static_ptr[dev];
+    return KHOP_OK;
+}
+
+// noin bitmap from a 32-bit CSC (or all zero without one).
+__global__ void static_noin_kernel(const uint32_t *cp, uint64_t n, uint32_t nw, uint32_t *noin) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw; i += stride) {
+        uint32_t w = 0;
+        if (cp)
+            for (int l = 0; l < 32; ++l) {
+                const uint64_t v = (i << 5) + l;
+                if (v < n && cp[v + 1] == cp[v]) w |= 1u << l;
+            }
+        noin[i] = w;
+    }
+}
+
+}  // namespace
+}  // namespace khop
+
+extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint32_t *col_idx,
+                                 const uint32_t *col_ptr, const uint32_t *row_idx, uint64_t nnz,
+                                 const uint32_t *seeds, uint64_t nseeds, uint32_t k,
+                                 uint64_t *out_counts, void *stream) {
+    using namespace khop;
+    if (n == 0 || n > kStaticMaxN || nnz > kStaticMaxNnz) return KHOP_EINVAL;
+    if (!row_ptr || (nnz && !col_idx) || (!col_ptr) != (!row_idx)) return KHOP_EINVAL;
+    if (nseeds == 0) return KHOP_OK;
+    if (!seeds || !out_counts) return KHOP_EINVAL;
+    uint32_t *base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc != KHOP_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    const uint32_t nw = (uint32_t)((n + 31) / 32);
+    const bool has_csc = col_ptr != nullptr;
+    PlainArgs<uint32_t> a;
+    a.n = n;
+    a.nnz = nnz;
+    a.n_noin = 0;
+    a.nw = nw;
+    a.symmetric = (has_csc && col_ptr == row_ptr && row_idx == col_idx) ? 1 : 0;
+    a.rp = row_ptr;
+    a.ci = col_idx;
+    a.cp = has_csc ? col_ptr : row_ptr;
+    a.ri = has_csc ? row_idx : col_idx;
+    uint32_t *bits = base + kOffBits;
+    const uint64_t bw = round64(kStaticNw);
+    a.V0 = bits;
+    a.V1 = bits + bw;
+    a.F0 = bits + 2 * bw;
+    a.F1 = bits + 3 * bw;
+    a.F2 = bits + 4 * bw;
+    uint32_t *noin = bits + 5 * bw;
+    a.noin = noin;
+    const uint64_t qw = round64(kStaticMaxN);
+    a.Qpre0 = base + kOffQ;
+    a.Qpre1 = base + kOffQ + qw;
+    a.Qrs0 = base + kOffQ + 2 * qw;
+    a.Qrs1 = base + kOffQ + 3 * qw;
+    a.TF0 = base + kOffTF;
+    a.TF1 = base + kOffTF + round64(kStaticTF);
+    a.ctl = (CtlBlock *)(base + kOffCtl);
+    a.seeds = seeds;
+    a.ks = nullptr;
+    a.k_all = k;
+    a.nq = nseeds;
+    a.out = out_counts;
+    a.out_te = nullptr;
+    a.stats = nullptr;
+    a.per_hop = nullptr;
+    a.hop_stride = 0;
+    a.direction = has_csc ? KHOP_DIR_AUTO : KHOP_DIR_PUSH;
+    a.alpha = 14.0f;
+    a.beta = 24.0f;
+    a.tile_log2 = 11;   // 2048-edge push tiles
+    uint32_t bl = 0;
+    for (uint64_t x = n; x; x >>= 1) ++bl;
+    a.ebits = 64 - bl;
+    a.stage = 1;
+    a.pull_cap = has_csc ? std::min<uint64_t>(n, (uint64_t)std::ceil((double)n / 24.0) + 32) : 0ull;
+    a.timeout_ns = 2000000000ull;
+
+    static_noin_kernel<<<nsm * 4, 256, 0, st>>>(col_ptr, n, nw, noin);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    constexpr int kBlk = 512;
+    const size_t smem = (2 * ((size_t(1) << a.tile_log2) + 2) + 3 * (size_t)kStage) * sizeof(uint32_t);
+    const void *fn = (const void *)plain_kernel<uint32_t, kBlk>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int grid = 0;
+    rc = cooperative_grid(fn, kBlk, smem, 2, nsm, &grid);
+    if (rc != KHOP_OK) return rc;
+    e = cudaMemsetAsync(a.ctl, 0, sizeof(CtlBlock), st);   // counters, barrier and error word
+    if (e != cudaSuccess) return cuda_status(e);
+    void *args[] = {(void *)&a};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlk), args, smem, st);
+    return cuda_status(e);
+}

@@ -36,7 +36,7 @@ EXPORTS = [
     "khop_strerror", "khop_version",
     "khop_graph_create", "khop_graph_destroy", "khop_graph_info", "khop_graph_device_bytes",
     "khop_graph_get_tuning", "khop_graph_set_tuning", "khop_autotune",
-    "khop_count", "khop_count_mixed", "khop_count_ex", "khop_get_error",
+    "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
     "khop_server_create", "khop_submit", "khop_poll", "khop_server_stats",
     "khop_server_destroy",
 ]
@@ -103,6 +103,7 @@ def lib():
                 "khop_count": (i32, [vp, vp, u64, u32, vp, vp]),
                 "khop_count_mixed": (i32, [vp, vp, vp, u64, vp, i32, vp]),
                 "khop_count_ex": (i32, [vp, vp, vp, u64, vp, vp, vp, vp, u32, vp]),
+                "khop_count_static": (i32, [u64, vp, vp, vp, vp, u64, vp, u64, u32, vp, vp]),
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
                 "khop_server_create": (i32, [ctypes.POINTER(khop_server_opts), ctypes.POINTER(vp)]),
                 "khop_submit": (i32, [vp, vp, u32, u32, ctypes.POINTER(u64)]),
@@ -189,6 +190,12 @@ def khop_count_ex(g, seeds, ks, nseeds, out_counts, out_te, out_stats, per_hop, 
                   stream) -> None:
     check(lib().khop_count_ex(g, seeds, ks, nseeds, out_counts, out_te, out_stats, per_hop,
                               hop_stride, stream), "khop_count_ex")
+
+
+def khop_count_static(n, row_ptr, col_idx, col_ptr, row_idx, nnz, seeds, nseeds, k,
+                      out_counts, stream) -> None:
+    check(lib().khop_count_static(n, row_ptr, col_idx, col_ptr, row_idx, nnz, seeds, nseeds, k,
+                                  out_counts, stream), "khop_count_static")
 
 
 def khop_get_error(g) -> int:
