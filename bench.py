@@ -198,6 +198,66 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak):
+    """The batched multi-source form: 4096 seeds (seed 2) with k uniform over
+    {1,2,3,6}, 64 queries per uint64 lane word, one persistent launch per
+    step.  Compared with the plain single-query path on the same queries."""
+    nq = 4096
+    seeds = gen.seeds(g, nq, seed=2)
+    ks = gen.mixed_ks(nq, seed=2)
+    d_s = torch.from_numpy(seeds.view(np.int32)).to(dev)
+    d_k = torch.from_numpy(ks.view(np.int32)).to(dev)
+    d_o = torch.empty(nq, dtype=torch.int64, device=dev)
+    d_p = torch.empty(nq, dtype=torch.int64, device=dev)
+    d_te = torch.empty(nq, dtype=torch.int64, device=dev)
+
+    def step():
+        kh.khop_count_mixed(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_o.data_ptr(),
+                            kh.MODE_BATCHED64, stream.cuda_stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ms, byts = [], 0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        byts += kh.khop_batch_stats(G.handle)["bytes"]
+    st = kh.khop_batch_stats(G.handle)
+    got = kh.as_u64(d_o).copy()
+    # the plain path on the same queries (one pass), with TE for GTEPS
+    flush.fill_(7)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    kh.khop_count_ex(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_p.data_ptr(),
+                     d_te.data_ptr(), None, None, 0, stream.cuda_stream)
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+    if not np.array_equal(got, kh.as_u64(d_p)):
+        raise SystemExit("batched counts differ from the plain path")
+    te = int(kh.as_u64(d_te).sum())
+    t = sum(ms) * 1e-3
+    achieved = byts / t / 1e9
+    return {"workload": "kronecker-s21-ef16-sym, 4096 seeds (seed 2), k uniform over {1,2,3,6}, "
+                        "64 queries per uint64 lane word, persistent launch",
+            "value": nq * steps / t, "unit": "queries/s", "ms_per_step": float(np.mean(ms)),
+            "gteps": te * steps / t / 1e9,
+            "plain_same_queries": {"value": nq / (plain_ms * 1e-3), "unit": "queries/s",
+                                   "ms": plain_ms},
+            "speedup_vs_plain": (nq * steps / t) / (nq / (plain_ms * 1e-3)),
+            "batches_per_step": st["batches"], "rounds_per_step": st["rounds"],
+            "pull_rounds_per_step": st["pull_rounds"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +267,10 @@ def main():
     ap.add_argument("--scale", type=int, default=21)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="plain path only")
+    ap.add_argument("--case", choices=["plain6", "batch6"],
+                    help="run one launch of a small case (for a profiler) and exit: plain6 = "
+                         "10 six-hop queries on the plain path, batch6 = 128 six-hop queries "
+                         "(two 64-lane batches)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -229,6 +293,15 @@ def main():
     seeds, ks = paper_queries(g)
     nq = seeds.size
     G = kh.Graph.from_csr(g)
+    if args.case:
+        cs = gen.seeds(g, 128 if args.case == "batch6" else 10, seed=2)
+        out = G.count_mixed(cs, np.full(cs.size, 6, np.uint32),
+                            mode=kh.MODE_BATCHED64 if args.case == "batch6" else kh.MODE_PLAIN)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "queries": int(cs.size),
+                          "counts_head": kh.as_u64(out)[:4].tolist()}))
+        G.close()
+        return 0
     stream = torch.cuda.current_stream()
     d_seeds = torch.from_numpy(seeds.view(np.int32)).to(dev)
     d_ks = torch.from_numpy(ks.view(np.int32)).to(dev)
@@ -321,6 +394,9 @@ def main():
                 "peak_kind": peak_kind}
 
     extras = {}
+    if not args.no_extras:
+        extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
+                                        flush, peak)
     lat_p = percentiles(lat)
     line = {
         "metric": "k-hop queries/sec (plain sequential, paper protocol)",
@@ -337,7 +413,7 @@ def main():
         "latency_us_by_k": {str(k): percentiles(v) for k, v in lat_by_k.items()},
         "e2e": e2e,
         "roofline": roofline,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps,   # one persistent plain_kernel launch per step
         "clocks": clocks,
     }
     line.update(extras)

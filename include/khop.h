@@ -169,6 +169,16 @@ enum khop_mode {
 int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
                      uint64_t nseeds, uint64_t *out_counts, int mode, void *stream);
 
+/*
+ * Counters of the last batched (KHOP_MODE_BATCHED64) launch on g: 64-lane
+ * batches run, algorithmic HBM bytes (the method's compulsory traffic: lane
+ * words of the vertices and frontier items touched, edge indices read,
+ * harvest sweeps), rounds and pull rounds.  Synchronises the device.  Any
+ * pointer may be NULL.
+ */
+int khop_batch_stats(khop_graph *g, uint64_t *batches, uint64_t *bytes, uint64_t *rounds,
+                     uint64_t *pull_rounds);
+
 /* Per-query record of the plain path (device memory, filled by khop_count_ex). */
 typedef struct {
     uint64_t t_start_ns;   /* %globaltimer when the query's first round began  */

@@ -59,4 +59,21 @@ int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, u
     return rc;
 }
 
+int khop_batch_stats(khop_graph *g, uint64_t *batches, uint64_t *bytes, uint64_t *rounds,
+                     uint64_t *pull_rounds) {
+    if (!g) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(g->mu);
+    unsigned long long v[4] = {0, 0, 0, 0};
+    if (g->batch.ctl) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(v, g->batch.ctl->pad, sizeof(v), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (batches) *batches = v[0];
+    if (bytes) *bytes = v[1];
+    if (rounds) *rounds = v[2];
+    if (pull_rounds) *pull_rounds = v[3];
+    return KHOP_OK;
+}
+
 }  // extern "C"

@@ -29,7 +29,10 @@ enum { DIR_PUSH = 0, DIR_PULL = 1 };
 constexpr int kBuckets = 64;         // batches are formed per bucket min(k, 63)
 constexpr int kBlock = 512;          // threads per CTA of the batched kernels
 constexpr int kPushUnroll = 4;
-constexpr int kFlatILP = 4;
+constexpr int kPullILP = 4;          // in-edge loads in flight per lane in a pull round
+constexpr int kLaneEdges = 8;        // in-edges a lane scans alone before the warp helps
+constexpr int kDeferEdges = 4096;    // longer in-lists go to the chunked pass
+constexpr int kChunk = 4096;         // in-edges per chunk of the chunked pass
 constexpr int kPlanes = 8;           // bit-sliced counter planes (up to 255 additions)
 constexpr int kStage = 2048;
 constexpr int kStagePosShift = 40;
@@ -58,6 +61,13 @@ struct BatchArgs {
     uint64_t *out;
     const uint32_t *order;       // 64 query indices per batch (kEmpty = unused lane)
     const unsigned long long *nbatches;
+    uint32_t *hv;                // deferred pull vertices
+    E *hend;
+    unsigned long long *hneed, *hacc;
+    uint64_t hcap;
+    uint32_t *ch_item;           // chunks of the deferred in-lists
+    E *ch_start;
+    uint64_t ccap;
     float alpha, beta;
     uint32_t tile_log2, ebits;
     int stage;
@@ -71,10 +81,10 @@ __device__ __forceinline__ T sel3(T x0, T x1, T x2, unsigned i) {
 }
 
 struct Shared {
-    unsigned long long cnt, mf, stage, limit, gbase;
+    unsigned long long cnt, mf, stage, limit, gbase, scan, unv;
     unsigned long long skipped;  // items not queued because the queue was past its cap
     int qfull;                   // this CTA saw the queue past its cap (pull rounds)
-    unsigned long long slot[4];
+    unsigned long long slot[8];
     int flag;
     // lane table of the current batch
     uint32_t seed[64];
@@ -183,8 +193,10 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E> &a, const Round<E
         sh.skipped = 0;
         sh.qfull = 0;
         if (sh.cnt) atomicAdd(slot_out + 1, sh.cnt);
+        if (sh.scan) atomicAdd(slot_out + 2, sh.scan);
         if (sh.mf) atomicAdd(slot_out + 3, sh.mf);
-        sh.cnt = sh.mf = 0;
+        if (sh.unv) atomicAdd(slot_out + 4, sh.unv);
+        sh.cnt = sh.mf = sh.scan = sh.unv = 0;
         sh.stage = 0;
         sh.limit = ~0ull;
         sh.flag = (int)nst;
@@ -284,31 +296,38 @@ __device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E>
     }
 }
 
-// Pull round: thread per vertex.  need = act & ~V[v]; the vertex ORs the
-// frontier lanes F_in[u] of its in-neighbours until every needed lane is
-// covered.  The first two in-edges are checked by the vertex's own lane;
-// the rest of the still-unresolved in-edge lists of a warp are scanned as
-// one flattened list, the hits OR-ed into a per-warp shared accumulator.
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
+    const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
+    const unsigned hi = __reduce_or_sync(FULL, (unsigned)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Pull round, sweep part.  Thread per vertex: need = act & ~V[v] (vertices
+// without in-edges are skipped); the vertex ORs the frontier lanes F_in[u]
+// of its in-neighbours until every needed lane is covered.  A lane first
+// scans up to kLaneEdges in-edges itself (kPullILP loads in flight); the
+// warp then takes the unresolved vertices one at a time, 32 * kPullILP
+// in-edges per step, OR-reducing across the warp.  In-lists with more than
+// kDeferEdges edges left are deferred to the chunked pass (pull_heavy).
 template <typename E>
 __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E> &R, Shared &sh,
-                                           E *s_winc, E *s_wpos, unsigned long long *s_acc,
-                                           uint32_t *st_w, E *st_pre, E *st_d) {
+                                           uint32_t *st_w, E *st_pre, E *st_d,
+                                           unsigned long long *slot) {
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    E *winc = s_winc + wib * 32;
-    E *wpos = s_wpos + wib * 32;
-    unsigned long long *wacc = s_acc + wib * 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
+    uint64_t scanned = 0, unv = 0;
     for (uint64_t i = gwarp; i < a.nw; i += nwarps) {
         const uint64_t v = (i << 5) + (uint64_t)lane;
         const uint32_t ni = a.noin[i];
         unsigned long long need = 0;
         if (v < a.n && !((ni >> lane) & 1u)) need = R.act & ~a.V[v];
-        if (__ballot_sync(FULL, need != 0ull) == 0u) {
+        const unsigned nmask = __ballot_sync(FULL, need != 0ull);
+        if (nmask == 0u) {
             if (v < a.n) R.Fout[v] = 0ull;
             continue;
         }
+        unv += __popc(nmask);
         E b = 0, e = 0;
         if (need) {
             b = a.cp[v];
@@ -316,55 +335,67 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
         }
         unsigned long long acc = 0;
         E pos = b;
-        {
-            const bool l0 = need && pos < e, l1 = l0 && pos + 1 < e;
-            const uint32_t u0 = l0 ? a.ri[pos] : 0u, u1 = l1 ? a.ri[pos + 1] : 0u;
-            if (l0) acc |= R.Fin[u0];
-            if (l1) acc |= R.Fin[u1];
-            pos += (E)l0 + (E)l1;
-        }
-        E rem = (need && (acc & need) != need) ? e - pos : (E)0;
-        while (__any_sync(FULL, rem > 0)) {
-            const E incl = warp_inclusive_sum(rem);
-            const E total = __shfl_sync(FULL, incl, 31);
-            const E excl = incl - rem;
-            winc[lane] = incl;
-            wpos[lane] = pos - excl;
-            wacc[lane] = 0ull;
-            __syncwarp();
-            const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
-            uint32_t uu[kFlatILP];
-            int own[kFlatILP];
+        for (int it = 0; it < kLaneEdges / kPullILP; ++it) {
+            const bool go = need && pos < e && (acc & need) != need;
+            if (!__any_sync(FULL, go)) break;
+            uint32_t u[kPullILP];
 #pragma unroll
-            for (int t = 0; t < kFlatILP; ++t) {
-                const uint32_t x = (uint32_t)(t * 32 + lane);
-                own[t] = -1;
-                uu[t] = 0;
-                if (x < chunk) {
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
-                    }
-                    own[t] = lo;
-                    uu[t] = a.ri[wpos[lo] + (E)x];
-                }
+            for (int t = 0; t < kPullILP; ++t) u[t] = (go && pos + t < e) ? a.ri[pos + t] : kEmpty;
+#pragma unroll
+            for (int t = 0; t < kPullILP; ++t)
+                if (u[t] != kEmpty) acc |= R.Fin[u[t]];
+            if (go) {
+                const E took = min((E)kPullILP, e - pos);
+                pos += took;
+                scanned += (uint64_t)took;
             }
-#pragma unroll
-            for (int t = 0; t < kFlatILP; ++t)
-                if (own[t] >= 0) {
-                    const unsigned long long f = R.Fin[uu[t]];
-                    if (f) atomicOr(&wacc[own[t]], f);
-                }
-            __syncwarp();
-            acc |= wacc[lane];
-            const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
-            pos += consumed;
-            rem -= consumed;
-            if ((acc & need) == need) rem = 0;
-            __syncwarp();
         }
-        const unsigned long long nb = acc & need;
+        const bool open = need && pos < e && (acc & need) != need;
+        const bool defer = open && (uint64_t)(e - pos) > (uint64_t)kDeferEdges;
+        unsigned todo = __ballot_sync(FULL, open && !defer);
+        while (todo) {
+            const int L = __ffs(todo) - 1;
+            const E vb = __shfl_sync(FULL, pos, L), ve = __shfl_sync(FULL, e, L);
+            const unsigned long long nd = __shfl_sync(FULL, need, L);
+            const unsigned long long a0 = __shfl_sync(FULL, acc, L);
+            unsigned long long wacc = 0;
+            for (E c = vb; c < ve; c += (E)(32 * kPullILP)) {
+                uint32_t u[kPullILP];
+#pragma unroll
+                for (int t = 0; t < kPullILP; ++t) {
+                    const E idx = c + (E)(t * 32 + lane);
+                    u[t] = idx < ve ? a.ri[idx] : kEmpty;
+                }
+#pragma unroll
+                for (int t = 0; t < kPullILP; ++t)
+                    if (u[t] != kEmpty) wacc |= R.Fin[u[t]];
+                if (lane == 0) scanned += (uint64_t)min((E)(32 * kPullILP), ve - c);
+                if (((warp_or64(wacc) | a0) & nd) == nd) break;
+            }
+            const unsigned long long fin = warp_or64(wacc) | a0;
+            if (lane == L) acc = fin;
+            todo &= todo - 1u;
+        }
+        if (defer) {
+            // the chunked pass finishes this vertex after the sweep
+            const unsigned long long h = atomicAdd(slot + 5, 1ull);
+            const uint64_t rest = (uint64_t)(e - pos);
+            const uint64_t nch = (rest + kChunk - 1) / kChunk;
+            const unsigned long long c0 = atomicAdd(slot + 6, (unsigned long long)nch);
+            if (h < a.hcap && c0 + nch <= a.ccap) {
+                a.hv[h] = (uint32_t)v;
+                a.hend[h] = e;
+                a.hneed[h] = need;
+                a.hacc[h] = acc;
+                for (uint64_t c = 0; c < nch; ++c) {
+                    a.ch_item[c0 + c] = (uint32_t)h;
+                    a.ch_start[c0 + c] = pos + (E)(c * kChunk);
+                }
+            } else {
+                atomicOr(&a.ctl->err, (unsigned)KHOP_DEVERR_CAPACITY);
+            }
+        }
+        const unsigned long long nb = defer ? 0ull : (acc & need);
         if (v < a.n) {
             R.Fout[v] = nb;
             if (nb) a.V[v] |= nb;
@@ -372,6 +403,78 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
         E d = 0;
         if (nb && !R.last) d = a.symmetric ? e - b : a.rp[v + 1] - a.rp[v];
         record(a, R, nb != 0ull && d > 0, (uint32_t)v, d, sh, st_w, st_pre, st_d);
+    }
+    scanned = warp_sum(scanned);
+    if (lane == 0) {
+        if (scanned) atomicAdd(&sh.scan, (unsigned long long)scanned);
+        if (unv) atomicAdd(&sh.unv, (unsigned long long)unv);   // lane 0 counted whole words
+    }
+}
+
+// Pull round, chunked pass over the deferred long in-lists: one warp per
+// chunk of kChunk in-edges; each chunk's lane OR goes to its vertex's
+// accumulator, and a chunk is skipped once its vertex has every needed lane.
+template <typename E>
+__device__ __forceinline__ void pull_chunks(const BatchArgs<E> &a, const Round<E> &R,
+                                            uint64_t nchunks, Shared &sh) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
+    uint64_t scanned = 0;
+    for (uint64_t c = gwarp; c < nchunks; c += nwarps) {
+        const uint32_t h = a.ch_item[c];
+        const unsigned long long nd = a.hneed[h];
+        if ((ld_relaxed_u64(&a.hacc[h]) & nd) == nd) continue;
+        const E cb = a.ch_start[c];
+        const E ce = min(cb + (E)kChunk, a.hend[h]);
+        unsigned long long wacc = 0;
+        int steps = 0;
+        for (E x = cb; x < ce; x += (E)(32 * kPullILP)) {
+            uint32_t u[kPullILP];
+#pragma unroll
+            for (int t = 0; t < kPullILP; ++t) {
+                const E idx = x + (E)(t * 32 + lane);
+                u[t] = idx < ce ? a.ri[idx] : kEmpty;
+            }
+#pragma unroll
+            for (int t = 0; t < kPullILP; ++t)
+                if (u[t] != kEmpty) wacc |= R.Fin[u[t]];
+            if (lane == 0) scanned += (uint64_t)min((E)(32 * kPullILP), ce - x);
+            if ((++steps & 7) == 0 &&
+                ((warp_or64(wacc) | ld_relaxed_u64(&a.hacc[h])) & nd) == nd)
+                break;
+        }
+        const unsigned long long fin = warp_or64(wacc);
+        if (lane == 0 && (fin & nd)) atomicOr(&a.hacc[h], fin & nd);
+    }
+    scanned = warp_sum(scanned);
+    if (lane == 0 && scanned) atomicAdd(&sh.scan, (unsigned long long)scanned);
+}
+
+// Pull round, last part: settle the deferred vertices (thread per item).
+template <typename E>
+__device__ __forceinline__ void pull_settle(const BatchArgs<E> &a, const Round<E> &R,
+                                            uint64_t nitems, Shared &sh, uint32_t *st_w,
+                                            E *st_pre, E *st_d) {
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t iters = (nitems + gthreads - 1) / gthreads;   // uniform: record() is warp-wide
+    for (uint64_t it = 0; it < iters; ++it) {
+        const uint64_t h = gtid + it * gthreads;
+        unsigned long long nb = 0;
+        uint32_t v = 0;
+        E d = 0;
+        if (h < nitems) {
+            v = a.hv[h];
+            nb = a.hacc[h] & a.hneed[h];
+            a.hacc[h] = 0ull;
+            R.Fout[v] = nb;
+            if (nb) {
+                a.V[v] |= nb;
+                if (!R.last) d = a.rp[v + 1] - a.rp[v];
+            }
+        }
+        record(a, R, nb != 0ull && d > 0, v, d, sh, st_w, st_pre, st_d);
     }
 }
 
@@ -437,15 +540,13 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     E *st_pre = (E *)(st_w + kStage);                                // [kStage]
     E *st_d = st_pre + kStage;                                       // [kStage]
     __shared__ Shared sh;
-    __shared__ E s_winc[kBlock], s_wpos[kBlock];
-    __shared__ unsigned long long s_acc[kBlock];
     __shared__ unsigned s_lane[64];
 
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
     unsigned long long *slots = (unsigned long long *)a.ctl->slot;
     if (threadIdx.x == 0) {
-        sh.cnt = sh.mf = sh.stage = 0;
+        sh.cnt = sh.mf = sh.stage = sh.scan = sh.unv = 0;
         sh.limit = ~0ull;
         sh.skipped = 0;
         sh.qfull = 0;
@@ -459,6 +560,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
     const uint64_t nb_total = *a.nbatches;
     uint64_t rdone = 0;
+    uint64_t bytes = 0, nrounds = 0, npull = 0;   // algorithmic HBM bytes, rounds run
     for (uint64_t b = 0; b < nb_total; ++b) {
         // lane table
         if (threadIdx.x < 64) {
@@ -509,9 +611,13 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             unsigned long long *Fz = sel3(a.F0, a.F1, a.F2, izero);
             for (uint64_t v = gtid; v < a.n; v += gthreads) Fz[v] = 0ull;
             if (gtid == 0) {
-                slots[4 * izero + 0] = 0ull;
-                slots[4 * izero + 1] = 0ull;
-                slots[4 * izero + 3] = 0ull;
+                slots[kSlotWords * izero + 0] = 0ull;
+                slots[kSlotWords * izero + 1] = 0ull;
+                slots[kSlotWords * izero + 2] = 0ull;
+                slots[kSlotWords * izero + 3] = 0ull;
+                slots[kSlotWords * izero + 4] = 0ull;
+                slots[kSlotWords * izero + 5] = 0ull;
+                slots[kSlotWords * izero + 6] = 0ull;
             }
             Round<E> R;
             R.first = r == 1;
@@ -525,24 +631,47 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             R.Q_out = qout ? a.Q1 : a.Q0;
             R.Qpre_out = qout ? a.Qpre1 : a.Qpre0;
             R.TF_out = qout ? a.TF1 : a.TF0;
-            R.qpack_out = slots + 4 * iout;
+            R.qpack_out = slots + kSlotWords * iout;
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
             R.items_in = items;
             R.mf = mf;
             if (dir == DIR_PUSH)
                 push_round<E>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d);
-            else
-                pull_round<E>(a, R, sh, s_winc, s_wpos, s_acc, st_w, st_pre, st_d);
-            flush_round<E>(a, R, sh, st_w, st_pre, st_d, slots + 4 * iout);
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + 4 * iout, sh.slot, 4,
+            else {
+                pull_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+                // deferred long in-lists (counts read after a barrier: uniform)
+                if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout + 5,
+                                  sh.slot + 5, 2, a.timeout_ns))
+                    return;
+                const uint64_t nitems = min((uint64_t)sh.slot[5], a.hcap);
+                if (nitems) {
+                    pull_chunks<E>(a, R, min((uint64_t)sh.slot[6], a.ccap), sh);
+                    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0,
+                                      a.timeout_ns))
+                        return;
+                    pull_settle<E>(a, R, nitems, sh, st_w, st_pre, st_d);
+                }
+            }
+            flush_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout, sh.slot, 5,
                               a.timeout_ns))
                 return;
+            const uint64_t W = sizeof(E);
+            const uint64_t items_out = last ? 0 : min((uint64_t)(sh.slot[0] >> a.ebits), R.cap);
+            if (dir == DIR_PUSH)
+                bytes += items * (4 + 2 * W + 8) + 12ull * R.mf + items_out * (4 + W);
+            else
+                bytes += 16ull * a.n + 4ull * a.nw + 2 * W * sh.slot[4] + 12ull * sh.slot[2] +
+                         items_out * (4 + W);
+            ++nrounds;
+            if (dir == DIR_PULL) ++npull;
             nf = sh.slot[1];
             items = sh.slot[0] >> a.ebits;
             mf = last ? 0 : sh.slot[3];
             prev = dir;
         }
         // harvest the lane counts, clear V
+        bytes += 16ull * a.n;
         unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * 64;
         harvest(a.V, a.n, part + (uint64_t)blockIdx.x * 64, s_lane);
         if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
@@ -562,6 +691,11 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             }
         }
         __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->pad[1] = bytes;
+        a.ctl->pad[2] = nrounds;
+        a.ctl->pad[3] = npull;
     }
 }
 
@@ -665,6 +799,14 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     a.out = out;
     a.order = bs.order;
     a.nbatches = (const unsigned long long *)&bs.ctl->pad[0];
+    a.hv = bs.hv;
+    a.hend = (E *)bs.hend;
+    a.hneed = bs.hneed;
+    a.hacc = bs.hacc;
+    a.hcap = bs.hcap;
+    a.ch_item = bs.ch_item;
+    a.ch_start = (E *)bs.ch_start;
+    a.ccap = bs.ccap;
     a.alpha = g->tune.batch_alpha;
     a.beta = g->tune.batch_beta;
     a.tile_log2 = tl;

@@ -284,6 +284,12 @@ void free_batch_state(BatchState &b) {
     cudaFree(b.ctl);
     cudaFree(b.part);
     cudaFree(b.order);
+    cudaFree(b.hv);
+    cudaFree(b.hend);
+    cudaFree(b.hneed);
+    cudaFree(b.hacc);
+    cudaFree(b.ch_item);
+    cudaFree(b.ch_start);
     b = BatchState{};
 }
 
@@ -300,6 +306,17 @@ int ensure_batch_state(khop_graph *g) {
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &b.ctl, 1);
     if (e == cudaSuccess) e = dalloc(g, &b.part, 2 * b.part_rows * 64);
+    // a deferred in-list has more than 4096 edges left, so at most nnz / 4096
+    // vertices defer per round, in at most 2 nnz / 4096 + 1 chunks of 4096
+    b.hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1);
+    b.ccap = 2 * (g->nnz / 4096) + 2;
+    if (e == cudaSuccess) e = dalloc(g, &b.hv, b.hcap);
+    if (e == cudaSuccess) e = dalloc_raw(g, &b.hend, b.hcap * g->ewidth);
+    if (e == cudaSuccess) e = dalloc(g, &b.hneed, b.hcap);
+    if (e == cudaSuccess) e = dalloc(g, &b.hacc, b.hcap);
+    if (e == cudaSuccess) e = dalloc(g, &b.ch_item, b.ccap);
+    if (e == cudaSuccess) e = dalloc_raw(g, &b.ch_start, b.ccap * g->ewidth);
+    if (e == cudaSuccess) e = cudaMemset(b.hacc, 0, b.hcap * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(b.V, 0, n * sizeof(uint64_t));
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(CtlBlock));

@@ -132,13 +132,17 @@ struct RoundSlot {
     unsigned long long nnew;      // vertices discovered
     unsigned long long scanned;   // in-edges examined by pull
     unsigned long long mf;        // out-edges of the vertices discovered
+    unsigned long long unv;       // vertices a pull round had to examine
+    unsigned long long pad[3];
 };
+constexpr int kSlotWords = sizeof(RoundSlot) / 8;
 
 // Small device control block of a traversal state (zeroed before a launch,
 // except `err`).
 struct CtlBlock {
     RoundSlot slot[3];
-    unsigned long long pad[4];
+    unsigned long long pad[4];      // batched path: [0] batches, [1] algorithmic bytes,
+                                    // [2] rounds, [3] pull rounds
     BarrierWords bar;
     unsigned err;                   // sticky khop_device_error bits
     unsigned pad2[31];
@@ -156,6 +160,14 @@ struct BatchState {
     uint64_t part_rows = 0;
     uint32_t *order = nullptr;                    // batch lane table (query indices)
     uint64_t order_cap = 0;
+    // pull rounds: vertices whose in-lists are finished in chunks
+    uint32_t *hv = nullptr;
+    void *hend = nullptr;                         // E
+    unsigned long long *hneed = nullptr, *hacc = nullptr;
+    uint64_t hcap = 0;
+    uint32_t *ch_item = nullptr;
+    void *ch_start = nullptr;                     // E
+    uint64_t ccap = 0;
     size_t bytes = 0;
 };
 

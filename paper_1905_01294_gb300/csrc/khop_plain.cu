@@ -533,10 +533,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             for (uint64_t i = gtid; i < a.nw; i += gthreads) Fz[i] = 0u;
             if (r == 1) prep_visited(a, Vnext, qn, gtid, gthreads);
             if (b0) {
-                slots[4 * izero + 0] = 0ull;
-                slots[4 * izero + 1] = 0ull;
-                slots[4 * izero + 2] = 0ull;
-                slots[4 * izero + 3] = 0ull;
+                slots[kSlotWords * izero + 0] = 0ull;
+                slots[kSlotWords * izero + 1] = 0ull;
+                slots[kSlotWords * izero + 2] = 0ull;
+                slots[kSlotWords * izero + 3] = 0ull;
+                slots[kSlotWords * izero + 4] = 0ull;
             }
             te += mf;
             Round<E> R;
@@ -552,14 +553,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.Qpre_out = qout ? a.Qpre1 : a.Qpre0;
             R.Qrs_out = qout ? a.Qrs1 : a.Qrs0;
             R.TF_out = qout ? a.TF1 : a.TF0;
-            R.qpack_out = slots + 4 * iout;
+            R.qpack_out = slots + kSlotWords * iout;
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
             R.items_in = items;
             R.mf = mf;
             if (dir == DIR_PUSH) push_round<E, BLOCK>(a, R, s_pre, s_rs, sh, st_pre, st_rs, st_d);
             else pull_round<E, BLOCK>(a, R, sh, s_winc, s_wpos, st_pre, st_rs, st_d);
-            flush_round<E, BLOCK>(a, R, sh, st_pre, st_rs, st_d, slots + 4 * iout);
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + 4 * iout, sh.slot, 4,
+            flush_round<E, BLOCK>(a, R, sh, st_pre, st_rs, st_d, slots + kSlotWords * iout);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout, sh.slot, 4,
                               a.timeout_ns))
                 return;
             const unsigned long long qp = sh.slot[0];

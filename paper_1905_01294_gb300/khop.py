@@ -37,6 +37,7 @@ EXPORTS = [
     "khop_graph_create", "khop_graph_destroy", "khop_graph_info", "khop_graph_device_bytes",
     "khop_graph_get_tuning", "khop_graph_set_tuning", "khop_autotune",
     "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
+    "khop_batch_stats",
     "khop_server_create", "khop_submit", "khop_poll", "khop_server_stats",
     "khop_server_destroy",
 ]
@@ -105,6 +106,8 @@ def lib():
                 "khop_count_ex": (i32, [vp, vp, vp, u64, vp, vp, vp, vp, u32, vp]),
                 "khop_count_static": (i32, [u64, vp, vp, vp, vp, u64, vp, u64, u32, vp, vp]),
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
+                "khop_batch_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                           ctypes.POINTER(u64), ctypes.POINTER(u64)]),
                 "khop_server_create": (i32, [ctypes.POINTER(khop_server_opts), ctypes.POINTER(vp)]),
                 "khop_submit": (i32, [vp, vp, u32, u32, ctypes.POINTER(u64)]),
                 "khop_poll": (i32, [vp, ctypes.POINTER(khop_result), u32, ctypes.POINTER(u32), i64]),
@@ -202,6 +205,13 @@ def khop_get_error(g) -> int:
     bits = ctypes.c_uint32()
     check(lib().khop_get_error(g, ctypes.byref(bits)), "khop_get_error")
     return bits.value
+
+
+def khop_batch_stats(g):
+    a, b, c, d = (ctypes.c_uint64() for _ in range(4))
+    check(lib().khop_batch_stats(g, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                 ctypes.byref(d)), "khop_batch_stats")
+    return dict(batches=a.value, bytes=b.value, rounds=c.value, pull_rounds=d.value)
 
 
 def khop_server_create(opts: khop_server_opts | None = None) -> int:

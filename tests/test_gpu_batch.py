@@ -131,3 +131,23 @@ def test_batched_equals_plain_on_scale21_mixed_workload():
     np.testing.assert_array_equal(got[idx], want)
     assert G.error_bits() == 0
     G.close()
+
+
+def test_long_in_lists_deferred_to_chunks():
+    """A hub with 10,000 in-edges that the lanes seeded in a separate cycle
+    never reach: with pull from round 2 on, every pull round scans the hub's
+    whole in-list for those lanes (the chunked path), and counts still match."""
+    L = 10000
+    hub = 0
+    leaves = np.arange(1, L + 1, dtype=np.uint32)
+    src = [leaves, np.array([hub, hub], np.uint32), leaves[:-1]]
+    dst = [np.full(L, hub, np.uint32), np.array([L + 1, 1], np.uint32), leaves[1:]]
+    cyc = np.arange(L + 2, L + 40, dtype=np.uint32)
+    src.append(cyc)
+    dst.append(np.append(cyc[1:], cyc[0]).astype(np.uint32))
+    g = gen.csr_from_edges(L + 40, np.concatenate(src), np.concatenate(dst))
+    seeds = np.concatenate([np.array([5, 17, 300, 9999, hub, L + 1], np.uint32),
+                            np.arange(L + 2, L + 40, dtype=np.uint32)])
+    ks = np.tile(np.array([1, 2, 3, 6, 9], np.uint32), len(seeds))[:len(seeds)]
+    for alpha in (1e-6, 14.0):
+        assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=1e-6) == 0
