@@ -165,6 +165,10 @@ enum khop_mode {
  * Per-seed k (ks[i] for seeds[i]).  In KHOP_MODE_BATCHED64 the queries are
  * grouped by k and packed 64 per uint64 lane word; every lane's result equals
  * the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
+ * After a first call with the same mode on g (which allocates the batch
+ * state), khop_count, khop_count_ex and khop_count_mixed issue only stream
+ * work, so they may be captured into a CUDA graph and replayed; the graph
+ * then owns the ordering of its launches.
  */
 int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
                      uint64_t nseeds, uint64_t *out_counts, int mode, void *stream);

@@ -741,37 +741,10 @@ __global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, cons
     }
 }
 
+// Kernel arguments over a batch state.
 template <typename E>
-int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
-                 uint64_t *out, cudaStream_t st) {
-    BatchState &bs = g->batch;
-    // order: nq plus up to 63 padding lanes per bucket
-    const uint64_t need = nq + 64ull * kBuckets;
-    if (bs.order_cap < need) {
-        cudaFree(bs.order);
-        bs.order = nullptr;
-        bs.order_cap = 0;
-        cudaError_t e = cudaMalloc(&bs.order, need * sizeof(uint32_t));
-        if (e != cudaSuccess) return cuda_status(e);
-        bs.order_cap = need;
-    }
-    uint32_t tl = 0;
-    while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
-    const size_t T2 = (size_t(1) << tl) + 2;
-    const size_t smem = T2 * (8 + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
-    const void *fn = (const void *)batch_kernel<E>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int grid = 0;
-    int rc = cooperative_grid(fn, kBlock, smem, 0, g->num_sms, &grid);
-    if (rc != KHOP_OK) return rc;
-    if ((uint64_t)grid > bs.part_rows) return KHOP_EINVAL;
-    e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
-    if (e != cudaSuccess) return cuda_status(e);
-    group_kernel<<<1, 1024, 0, st>>>(seeds, ks, nq, g->n, out, bs.order, bs.order_cap,
-                                     (unsigned long long *)&bs.ctl->pad[0], &bs.ctl->err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_status(e);
+BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, const uint32_t *ks,
+                       uint64_t *out, const uint32_t *order, const unsigned long long *nbatches) {
     BatchArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -797,8 +770,8 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     a.seeds = seeds;
     a.ks = ks;
     a.out = out;
-    a.order = bs.order;
-    a.nbatches = (const unsigned long long *)&bs.ctl->pad[0];
+    a.order = order;
+    a.nbatches = nbatches;
     a.hv = bs.hv;
     a.hend = (E *)bs.hend;
     a.hneed = bs.hneed;
@@ -809,14 +782,68 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     a.ccap = bs.ccap;
     a.alpha = g->tune.batch_alpha;
     a.beta = g->tune.batch_beta;
+    uint32_t tl = 0;
+    while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
     a.tile_log2 = tl;
     a.ebits = g->ebits;
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
     a.pull_cap = std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.batch_beta) + 32);
     a.timeout_ns = g->timeout_ns;
+    return a;
+}
+
+// Cooperative launch of the batch kernel over `bs`; grid_ctas = 0 fills the
+// GPU, otherwise at most that many CTAs (so that several run side by side).
+template <typename E>
+int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E> &a, int grid_ctas, cudaStream_t st) {
+    const size_t T2 = (size_t(1) << a.tile_log2) + 2;
+    const size_t smem = T2 * (8 + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
+    const void *fn = (const void *)batch_kernel<E>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int grid = 0;
+    int rc = cooperative_grid(fn, kBlock, smem, 0, g->num_sms, &grid);
+    if (rc != KHOP_OK) return rc;
+    if (grid_ctas > 0 && grid_ctas < grid) grid = grid_ctas;
+    if ((uint64_t)grid > bs.part_rows) return KHOP_EINVAL;
     void *args[] = {(void *)&a};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, st);
     return cuda_status(e);
+}
+
+template <typename E>
+int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
+                 uint64_t *out, cudaStream_t st) {
+    BatchState &bs = g->batch;
+    // order: nq plus up to 63 padding lanes per bucket
+    const uint64_t need = nq + 64ull * kBuckets;
+    if (bs.order_cap < need) {
+        cudaFree(bs.order);
+        bs.order = nullptr;
+        bs.order_cap = 0;
+        cudaError_t e = cudaMalloc(&bs.order, need * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_status(e);
+        bs.order_cap = need;
+    }
+    cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    group_kernel<<<1, 1024, 0, st>>>(seeds, ks, nq, g->n, out, bs.order, bs.order_cap,
+                                     (unsigned long long *)&bs.ctl->pad[0], &bs.ctl->err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchArgs<E> a = make_args<E>(g, bs, seeds, ks, out, bs.order,
+                                  (const unsigned long long *)&bs.ctl->pad[0]);
+    return launch_kernel<E>(g, bs, a, 0, st);
+}
+
+template <typename E>
+int slot_typed(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
+               int grid_ctas, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchArgs<E> a = make_args<E>(g, bs, lanes, lanes + 64, out, lanes + 128,
+                                  (const unsigned long long *)(lanes + 192));
+    return launch_kernel<E>(g, bs, a, grid_ctas, st);
 }
 
 }  // namespace
@@ -825,6 +852,12 @@ int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
                  uint64_t *out, cudaStream_t st) {
     if (g->ewidth == 4) return launch_typed<uint32_t>(g, seeds, ks, nq, out, st);
     return launch_typed<unsigned long long>(g, seeds, ks, nq, out, st);
+}
+
+int batch_launch_slot(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
+                      int grid_ctas, cudaStream_t st) {
+    if (g->ewidth == 4) return slot_typed<uint32_t>(g, bs, lanes, out, grid_ctas, st);
+    return slot_typed<unsigned long long>(g, bs, lanes, out, grid_ctas, st);
 }
 
 }  // namespace khop

@@ -253,13 +253,22 @@ int cuda_status(cudaError_t e) {
     return KHOP_ECUDA;
 }
 
+// Order a call after the previous call on g when it comes on another stream.
+// A stream being captured into a CUDA graph is left alone: its captured work
+// runs when the graph is launched, and ordering the launches is the caller's.
 int order_after_previous(khop_graph *g, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return KHOP_ECUDA;
+    if (cs != cudaStreamCaptureStatusNone) return KHOP_OK;
     if (g->have_last && g->last_stream != s)
         return cuda_status(cudaStreamWaitEvent(s, g->done, 0));
     return KHOP_OK;
 }
 
 int mark_done(khop_graph *g, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return KHOP_ECUDA;
+    if (cs != cudaStreamCaptureStatusNone) return KHOP_OK;
     cudaError_t e = cudaEventRecord(g->done, s);
     g->last_stream = s;
     g->have_last = true;
@@ -293,12 +302,17 @@ void free_batch_state(BatchState &b) {
     b = BatchState{};
 }
 
-int ensure_batch_state(khop_graph *g) {
-    BatchState &b = g->batch;
-    if (b.V) return KHOP_OK;
+// Allocate a bit-sliced batch state for graph g (no device sync needed by
+// the caller afterwards).  *bytes receives its size.
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes) {
     const uint64_t n = g->n;
     const uint64_t before = g->device_bytes;
+    b = BatchState{};
     b.part_rows = (uint64_t)g->num_sms * 4;
+    // a deferred in-list has more than 4096 edges left, so at most nnz / 4096
+    // vertices defer per round, in at most 2 nnz / 4096 + 1 chunks of 4096
+    b.hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1);
+    b.ccap = 2 * (g->nnz / 4096) + 2;
     cudaError_t e = dalloc(g, &b.V, n);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.Q[i], n);
@@ -306,10 +320,6 @@ int ensure_batch_state(khop_graph *g) {
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &b.ctl, 1);
     if (e == cudaSuccess) e = dalloc(g, &b.part, 2 * b.part_rows * 64);
-    // a deferred in-list has more than 4096 edges left, so at most nnz / 4096
-    // vertices defer per round, in at most 2 nnz / 4096 + 1 chunks of 4096
-    b.hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1);
-    b.ccap = 2 * (g->nnz / 4096) + 2;
     if (e == cudaSuccess) e = dalloc(g, &b.hv, b.hcap);
     if (e == cudaSuccess) e = dalloc_raw(g, &b.hend, b.hcap * g->ewidth);
     if (e == cudaSuccess) e = dalloc(g, &b.hneed, b.hcap);
@@ -327,7 +337,21 @@ int ensure_batch_state(khop_graph *g) {
         return cuda_status(e);
     }
     b.bytes = g->device_bytes - before;
+    if (bytes) *bytes = b.bytes;
     return KHOP_OK;
+}
+
+// Bytes a batch state of graph g takes (for admission decisions).
+uint64_t batch_state_bytes(const khop_graph *g) {
+    const uint64_t n = g->n, W = (uint64_t)g->ewidth;
+    const uint64_t hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1), ccap = 2 * (g->nnz / 4096) + 2;
+    return 4 * n * 8 + 2 * n * 4 + 2 * n * W + 2 * g->tf_cap * 4 + sizeof(CtlBlock) +
+           2 * (uint64_t)g->num_sms * 4 * 64 * 8 + hcap * (4 + W + 16) + ccap * (4 + W);
+}
+
+int ensure_batch_state(khop_graph *g) {
+    if (g->batch.V) return KHOP_OK;
+    return alloc_batch_state(g, g->batch, nullptr);
 }
 
 }  // namespace khop

@@ -217,6 +217,9 @@ int cuda_status(cudaError_t e);
 int order_after_previous(khop_graph *g, cudaStream_t s);   // call under g->mu
 int mark_done(khop_graph *g, cudaStream_t s);              // call under g->mu
 int ensure_batch_state(khop_graph *g);                     // call under g->mu
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes);  // a standalone state
+void free_batch_state(BatchState &b);
+uint64_t batch_state_bytes(const khop_graph *g);
 int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms,
                      int *grid);
 
@@ -228,5 +231,10 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
 // batched path (khop_batch.cu)
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st);
+// One batch of up to 64 lanes on a standalone state.  `lanes` (device,
+// 8-byte aligned) holds seeds[64], ks[64], the lane order[64] (query index or
+// 0xffffffff) and then the 64-bit batch count (1).
+int batch_launch_slot(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
+                      int grid_ctas, cudaStream_t st);
 
 }  // namespace khop

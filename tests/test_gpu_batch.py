@@ -151,3 +151,35 @@ def test_long_in_lists_deferred_to_chunks():
     ks = np.tile(np.array([1, 2, 3, 6, 9], np.uint32), len(seeds))[:len(seeds)]
     for alpha in (1e-6, 14.0):
         assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=1e-6) == 0
+
+
+def test_captured_cuda_graph_replays_batched_and_plain():
+    """Both paths captured in a CUDA graph (after a first direct call) and
+    replayed twice give the direct call's counts."""
+    g = gen.rmat(12, 16, seed=9, symmetrize=True)
+    G = kh.Graph.from_csr(g)
+    seeds = gen.seeds(g, 300, seed=1)
+    ks = gen.mixed_ks(300, seed=3)
+    s = torch.from_numpy(seeds.view(np.int32)).cuda()
+    k = torch.from_numpy(ks.view(np.int32)).cuda()
+    want, _ = oracle.khop_counts(g, seeds, ks)
+    for mode in (kh.MODE_BATCHED64, kh.MODE_PLAIN):
+        out = torch.zeros(300, dtype=torch.int64, device="cuda")
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            kh.khop_count_mixed(G.handle, s.data_ptr(), k.data_ptr(), 300, out.data_ptr(), mode,
+                                side.cuda_stream)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(kh.as_u64(out), want)
+        graph = torch.cuda.CUDAGraph()
+        out.zero_()
+        with torch.cuda.graph(graph, stream=side):
+            kh.khop_count_mixed(G.handle, s.data_ptr(), k.data_ptr(), 300, out.data_ptr(), mode,
+                                side.cuda_stream)
+        for _ in range(2):
+            out.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(kh.as_u64(out), want)
+    assert G.error_bits() == 0
+    G.close()

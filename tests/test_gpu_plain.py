@@ -265,3 +265,19 @@ def test_scale21_symmetric_sampled_in_bench_configuration():
         np.testing.assert_array_equal(got["te"], want_te)
     assert G.error_bits() == 0
     G.close()
+
+
+def test_autotune_changes_speed_only():
+    g = gen.rmat(13, 16, seed=4, symmetrize=True)
+    G = kh.Graph.from_csr(g)
+    seeds = gen.seeds(g, 32, seed=5)
+    before = kh.as_u64(G.count(seeds, 6))
+    t = G.autotune(seeds, 6)
+    assert t.block_threads in (256, 512, 1024) and t.push_tile in (512, 1024, 2048, 4096)
+    assert t.alpha > 0 and t.beta > 0 and t.batch_alpha > 0 and t.batch_beta > 0
+    want, _ = oracle.khop_counts(g, seeds, 6)
+    np.testing.assert_array_equal(before, want)
+    np.testing.assert_array_equal(kh.as_u64(G.count(seeds, 6)), want)
+    np.testing.assert_array_equal(
+        kh.as_u64(G.count_mixed(seeds, np.full(32, 6, np.uint32), mode=kh.MODE_BATCHED64)), want)
+    G.close()
