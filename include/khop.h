@@ -280,6 +280,14 @@ int khop_server_create(const khop_server_opts *opts, khop_server **out);
 int khop_submit(khop_server *s, khop_graph *g, uint32_t seed, uint32_t k, uint64_t *ticket);
 
 /*
+ * Queue `count` requests at once (host arrays seeds[i], ks[i]); tickets[i]
+ * receives each ticket.  All or nothing: EINVAL if any seed >= n, EBUSY if
+ * the queue cannot take them all.  Thread-safe.
+ */
+int khop_submit_many(khop_server *s, khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
+                     uint32_t count, uint64_t *tickets);
+
+/*
  * Take up to `max` finished results, waiting up to timeout_us (0 = do not
  * wait, < 0 = wait until at least one is available or the server stops).
  * *nout receives the number written.  Thread-safe.

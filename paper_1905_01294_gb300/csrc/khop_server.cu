@@ -362,6 +362,36 @@ int khop_submit(khop_server *s, khop_graph *g, uint32_t seed, uint32_t k, uint64
     return KHOP_OK;
 }
 
+int khop_submit_many(khop_server *s, khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
+                     uint32_t count, uint64_t *tickets) {
+    if (!s || !g || (count && (!seeds || !ks || !tickets))) return KHOP_EINVAL;
+    for (uint32_t i = 0; i < count; ++i)
+        if ((uint64_t)seeds[i] >= g->n) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return KHOP_ESHUTDOWN;
+    if (s->queued + count > s->opts.max_pending) return KHOP_EBUSY;
+    const uint64_t t = now_ns();
+    bool any = false;
+    for (uint32_t i = 0; i < count; ++i) {
+        Request r{s->next_ticket++, g, seeds[i], ks[i], t};
+        tickets[i] = r.ticket;
+        s->submitted++;
+        s->queued++;
+        if (ks[i] == 0) {
+            khop_result res{r.ticket, 0ull, KHOP_OK, 0u, t, now_ns()};
+            s->outbox.push_back(res);
+            s->completed++;
+            s->queued--;
+            continue;
+        }
+        s->inbox.push_back(r);
+        any = true;
+    }
+    if (any) s->cv_in.notify_one();
+    s->cv_out.notify_all();
+    return KHOP_OK;
+}
+
 int khop_poll(khop_server *s, khop_result *out, uint32_t max, uint32_t *nout, int64_t timeout_us) {
     if (!s || !nout || (max && !out)) return KHOP_EINVAL;
     *nout = 0;

@@ -38,7 +38,7 @@ EXPORTS = [
     "khop_graph_get_tuning", "khop_graph_set_tuning", "khop_autotune",
     "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
     "khop_batch_stats",
-    "khop_server_create", "khop_submit", "khop_poll", "khop_server_stats",
+    "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
     "khop_server_destroy",
 ]
 
@@ -110,6 +110,7 @@ def lib():
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]),
                 "khop_server_create": (i32, [ctypes.POINTER(khop_server_opts), ctypes.POINTER(vp)]),
                 "khop_submit": (i32, [vp, vp, u32, u32, ctypes.POINTER(u64)]),
+                "khop_submit_many": (i32, [vp, vp, vp, vp, u32, vp]),
                 "khop_poll": (i32, [vp, ctypes.POINTER(khop_result), u32, ctypes.POINTER(u32), i64]),
                 "khop_server_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -225,6 +226,15 @@ def khop_submit(s, g, seed, k) -> int:
     t = ctypes.c_uint64()
     check(lib().khop_submit(s, g, seed, k, ctypes.byref(t)), "khop_submit")
     return t.value
+
+
+def khop_submit_many(s, g, seeds, ks) -> np.ndarray:
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    ks = np.ascontiguousarray(np.broadcast_to(np.asarray(ks, np.uint32), seeds.shape))
+    tickets = np.empty(seeds.size, dtype=np.uint64)
+    check(lib().khop_submit_many(s, g, seeds.ctypes.data, ks.ctypes.data, seeds.size,
+                                 tickets.ctypes.data), "khop_submit_many")
+    return tickets
 
 
 def khop_poll(s, max_results: int, timeout_us: int):
@@ -411,8 +421,28 @@ class Server:
     def submit(self, graph: Graph, seed: int, k: int) -> int:
         return khop_submit(self.handle, graph.handle, int(seed), int(k))
 
+    def submit_many(self, graph: Graph, seeds, ks) -> np.ndarray:
+        return khop_submit_many(self.handle, graph.handle, seeds, ks)
+
     def poll(self, max_results=4096, timeout_us=0):
         return khop_poll(self.handle, max_results, timeout_us)
+
+    RESULT_DTYPE = np.dtype([("ticket", "u8"), ("count", "u8"), ("status", "i4"), ("k", "u4"),
+                             ("t_submit_ns", "u8"), ("t_done_ns", "u8")])
+
+    def poll_arrays(self, max_results=4096, timeout_us=0):
+        """Finished results as a numpy record array (ticket, count, status, k,
+        t_submit_ns, t_done_ns), at most max_results of them."""
+        buf = getattr(self, "_pollbuf", None)
+        if buf is None or buf.size < max_results:
+            buf = np.zeros(max_results, dtype=self.RESULT_DTYPE)
+            self._pollbuf = buf
+        n = ctypes.c_uint32()
+        rc = lib().khop_poll(self.handle, buf.ctypes.data_as(ctypes.POINTER(khop_result)),
+                             max_results, ctypes.byref(n), timeout_us)
+        if rc not in (OK, ETIMEDOUT):
+            raise KhopError(rc, "khop_poll")
+        return buf[:n.value].copy()
 
     def stats(self):
         return khop_server_stats(self.handle)
