@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--scale", type=int, default=21)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="plain path only")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
     ap.add_argument("--case", choices=["plain6", "batch6"],
                     help="run one launch of a small case (for a profiler) and exit: plain6 = "
                          "10 six-hop queries on the plain path, batch6 = 128 six-hop queries "
@@ -475,8 +476,9 @@ def main():
     if not args.no_extras:
         extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
                                         flush, peak)
-        mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
-        extras["serving"] = serving_leg(kh, G, g, mean_by_k)
+        if not args.no_serving:
+            mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
+            extras["serving"] = serving_leg(kh, G, g, mean_by_k)
     lat_p = percentiles(lat)
     line = {
         "metric": "k-hop queries/sec (plain sequential, paper protocol)",

@@ -551,15 +551,23 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
         sh.skipped = 0;
         sh.qfull = 0;
     }
-    // Launch prologue: frontier words zero.
-    for (uint64_t v = gtid; v < a.n; v += gthreads) {
-        a.F0[v] = 0ull;
-        a.F1[v] = 0ull;
-        a.F2[v] = 0ull;
-    }
+    // The frontier buffers rotate across launches: the buffer the next round
+    // writes was zeroed by the previous round, and V was cleared by the last
+    // harvest.  A launch that did not finish leaves `dirty` set, and the next
+    // one starts from zeroed buffers.  Both words are read before the
+    // prologue barrier and written only after it, so every CTA sees the same.
+    const bool dirty = ld_volatile_u32(&a.ctl->dirty) != 0u;
+    uint64_t rdone = dirty ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
+    if (dirty)
+        for (uint64_t v = gtid; v < a.n; v += gthreads) {
+            a.F0[v] = 0ull;
+            a.F1[v] = 0ull;
+            a.F2[v] = 0ull;
+            a.V[v] = 0ull;
+        }
     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+    if (gtid == 0) a.ctl->dirty = 1u;
     const uint64_t nb_total = *a.nbatches;
-    uint64_t rdone = 0;
     uint64_t bytes = 0, nrounds = 0, npull = 0;   // algorithmic HBM bytes, rounds run
     for (uint64_t b = 0; b < nb_total; ++b) {
         // lane table
@@ -696,6 +704,9 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
         a.ctl->pad[1] = bytes;
         a.ctl->pad[2] = nrounds;
         a.ctl->pad[3] = npull;
+        a.ctl->rdone = rdone;
+        __threadfence();
+        a.ctl->dirty = 0u;
     }
 }
 

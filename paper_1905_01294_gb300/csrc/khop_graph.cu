@@ -232,12 +232,8 @@ void free_graph(khop_graph *g) {
     if (g->ri && g->ri != g->ci) cudaFree(g->ri);
     cudaFree(g->rp);
     cudaFree(g->ci);
-    cudaFree(g->V);
-    cudaFree(g->V2);
     cudaFree(g->noin);
-    for (auto &f : g->F) cudaFree(f);
-    for (int i = 0; i < 2; ++i) { cudaFree(g->Qpre[i]); cudaFree(g->Qrs[i]); cudaFree(g->TF[i]); }
-    cudaFree(g->ctl);
+    free_plain_state(g->plain);
     free_batch_state(g->batch);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
@@ -302,6 +298,41 @@ void free_batch_state(BatchState &b) {
     b = BatchState{};
 }
 
+void free_plain_state(PlainState &p) {
+    cudaFree(p.V);
+    cudaFree(p.V2);
+    for (auto &f : p.F) cudaFree(f);
+    for (int i = 0; i < 2; ++i) { cudaFree(p.Qpre[i]); cudaFree(p.Qrs[i]); cudaFree(p.TF[i]); }
+    cudaFree(p.ctl);
+    p = PlainState{};
+}
+
+// Allocate (and zero) a plain traversal state for graph g; synchronises.
+int alloc_plain_state(khop_graph *g, PlainState &p) {
+    const uint64_t n = g->n, nw = g->nw;
+    const uint64_t before = g->device_bytes;
+    p = PlainState{};
+    cudaError_t e = dalloc(g, &p.V, nw);
+    if (e == cudaSuccess) e = dalloc(g, &p.V2, nw);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &p.F[i], nw);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &p.Qpre[i], n * (uint64_t)g->ewidth);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &p.Qrs[i], n * (uint64_t)g->ewidth);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &p.TF[i], g->tf_cap);
+    if (e == cudaSuccess) e = dalloc(g, &p.ctl, 1);
+    if (e == cudaSuccess) e = cudaMemset(p.V, 0, nw * 4);
+    if (e == cudaSuccess) e = cudaMemset(p.V2, 0, nw * 4);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(p.F[i], 0, nw * 4);
+    if (e == cudaSuccess) e = cudaMemset(p.ctl, 0, sizeof(CtlBlock));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plain_state(p);
+        g->device_bytes = before;
+        return cuda_status(e);
+    }
+    p.bytes = g->device_bytes - before;
+    return KHOP_OK;
+}
+
 // Allocate a bit-sliced batch state for graph g (no device sync needed by
 // the caller afterwards).  *bytes receives its size.
 int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes) {
@@ -347,6 +378,10 @@ uint64_t batch_state_bytes(const khop_graph *g) {
     const uint64_t hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1), ccap = 2 * (g->nnz / 4096) + 2;
     return 4 * n * 8 + 2 * n * 4 + 2 * n * W + 2 * g->tf_cap * 4 + sizeof(CtlBlock) +
            2 * (uint64_t)g->num_sms * 4 * 64 * 8 + hcap * (4 + W + 16) + ccap * (4 + W);
+}
+
+uint64_t plain_state_bytes(const khop_graph *g) {
+    return 5ull * g->nw * 4 + 4 * g->n * (uint64_t)g->ewidth + 2 * g->tf_cap * 4 + sizeof(CtlBlock);
 }
 
 int ensure_batch_state(khop_graph *g) {
@@ -472,17 +507,10 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
         if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
     }
 
-    // Plain traversal state.
+    // Plain traversal state and the in-edge-less vertex map.
     g->tf_cap = nnz / 256 + 2;
     const uint64_t nw = g->nw;
-    e = dalloc(g, &g->V, nw);
-    if (e == cudaSuccess) e = dalloc(g, &g->V2, nw);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &g->F[i], nw);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &g->Qpre[i], n * (uint64_t)g->ewidth);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &g->Qrs[i], n * (uint64_t)g->ewidth);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &g->TF[i], g->tf_cap);
-    if (e == cudaSuccess) e = dalloc(g, &g->ctl, 1);
-    if (e == cudaSuccess) e = dalloc(g, &g->noin, nw);
+    e = dalloc(g, &g->noin, nw);
     if (e == cudaSuccess) {
         unsigned long long *cnt = nullptr;
         e = cudaMalloc(&cnt, sizeof(unsigned long long));
@@ -500,12 +528,10 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
         g->n_noin = h;
         cudaFree(cnt);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->V, 0, nw * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->V2, 0, nw * 4, st);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(g->F[i], 0, nw * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl, 0, sizeof(CtlBlock), st);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
+    int prc = alloc_plain_state(g, g->plain);
+    if (prc != KHOP_OK) { free_graph(g); return prc; }
+    e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
     if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
 
     g->tune.direction = KHOP_DIR_AUTO;
@@ -575,10 +601,10 @@ int khop_get_error(khop_graph *g, uint32_t *bits) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_status(e);
     unsigned a = 0, b = 0;
-    e = cudaMemcpy(&a, &g->ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(&a, &g->plain.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && g->batch.ctl)
         e = cudaMemcpy(&b, &g->batch.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(&g->ctl->err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(&g->plain.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess && g->batch.ctl) e = cudaMemset(&g->batch.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     *bits = a | b;

@@ -144,8 +144,22 @@ struct CtlBlock {
     unsigned long long pad[4];      // batched path: [0] batches, [1] algorithmic bytes,
                                     // [2] rounds, [3] pull rounds
     BarrierWords bar;
+    // Kept across launches (a launch clears only what comes before `err`):
     unsigned err;                   // sticky khop_device_error bits
-    unsigned pad2[31];
+    unsigned dirty;                 // batched state may be dirty (a launch did not finish)
+    unsigned long long rdone;       // batched: rounds run so far (frontier buffer rotation)
+    unsigned pad2[28];
+};
+
+// Plain single-query traversal state (one query at a time).
+struct PlainState {
+    uint32_t *V = nullptr, *V2 = nullptr;         // visited bitmaps (queries alternate)
+    uint32_t *F[3] = {nullptr, nullptr, nullptr}; // frontier bitmaps, rotating per round
+    void *Qpre[2] = {nullptr, nullptr};           // queue: out-edge prefix (E)
+    void *Qrs[2] = {nullptr, nullptr};            // queue: row start (E)
+    uint32_t *TF[2] = {nullptr, nullptr};         // first queue item of each push tile
+    CtlBlock *ctl = nullptr;
+    uint64_t bytes = 0;
 };
 
 // Bit-sliced (64-lane) batch state of a graph.
@@ -187,16 +201,10 @@ struct khop_graph {
     void *cp = nullptr;
     uint32_t *ri = nullptr;
 
-    // plain single-query traversal state, device
-    uint32_t *V = nullptr, *V2 = nullptr;   // visited bitmaps (queries alternate)
     uint32_t *noin = nullptr;               // bit set: vertex has no in-edge
     uint64_t n_noin = 0;                    // vertices without in-edges
-    uint32_t *F[3] = {nullptr, nullptr, nullptr};
-    void *Qpre[2] = {nullptr, nullptr};
-    void *Qrs[2] = {nullptr, nullptr};
-    uint32_t *TF[2] = {nullptr, nullptr};
-    uint64_t tf_cap = 0;
-    khop::CtlBlock *ctl = nullptr;
+    uint64_t tf_cap = 0;                    // push-tile map entries
+    khop::PlainState plain;                 // plain single-query traversal state
 
     khop::BatchState batch;
 
@@ -218,8 +226,11 @@ int order_after_previous(khop_graph *g, cudaStream_t s);   // call under g->mu
 int mark_done(khop_graph *g, cudaStream_t s);              // call under g->mu
 int ensure_batch_state(khop_graph *g);                     // call under g->mu
 int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes);  // a standalone state
+int alloc_plain_state(khop_graph *g, PlainState &p);
+void free_plain_state(PlainState &p);
 void free_batch_state(BatchState &b);
 uint64_t batch_state_bytes(const khop_graph *g);
+uint64_t plain_state_bytes(const khop_graph *g);
 int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms,
                      int *grid);
 
@@ -227,6 +238,9 @@ int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm
 int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
                  uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st);
+// The same on a standalone state, with at most grid_ctas CTAs (0 = fill the GPU).
+int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
+                       uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st);
 
 // batched path (khop_batch.cu)
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,

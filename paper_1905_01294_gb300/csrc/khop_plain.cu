@@ -609,14 +609,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
 }
 
 template <typename E, int BLOCK>
-int launch_block(khop_graph *g, PlainArgs<E> &a, size_t smem, cudaStream_t st) {
+int launch_block(khop_graph *g, PlainArgs<E> &a, size_t smem, int grid_ctas, cudaStream_t st) {
     const void *fn = (const void *)plain_kernel<E, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     int grid = 0;
     int rc = cooperative_grid(fn, BLOCK, smem, g->tune.blocks_per_sm, g->num_sms, &grid);
     if (rc != KHOP_OK) return rc;
-    e = cudaMemsetAsync(g->ctl, 0, offsetof(CtlBlock, err), st);   // keeps the sticky err
+    if (grid_ctas > 0 && grid_ctas < grid) grid = grid_ctas;
+    e = cudaMemsetAsync(a.ctl, 0, offsetof(CtlBlock, err), st);   // keeps the sticky err
     if (e != cudaSuccess) return cuda_status(e);
     void *args[] = {(void *)&a};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, smem, st);
@@ -624,9 +625,10 @@ int launch_block(khop_graph *g, PlainArgs<E> &a, size_t smem, cudaStream_t st) {
 }
 
 template <typename E>
-int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
-                 uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
-                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st) {
+int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
+                 uint32_t k_all, uint64_t nq, uint64_t *out, uint64_t *out_te,
+                 khop_query_stats *stats, uint64_t *per_hop, uint32_t hop_stride, int grid_ctas,
+                 cudaStream_t st) {
     PlainArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -638,18 +640,18 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
     a.cp = (const E *)g->cp;
     a.ri = g->ri;
     a.noin = g->noin;
-    a.V0 = g->V;
-    a.V1 = g->V2;
-    a.F0 = g->F[0];
-    a.F1 = g->F[1];
-    a.F2 = g->F[2];
-    a.Qpre0 = (E *)g->Qpre[0];
-    a.Qpre1 = (E *)g->Qpre[1];
-    a.Qrs0 = (E *)g->Qrs[0];
-    a.Qrs1 = (E *)g->Qrs[1];
-    a.TF0 = g->TF[0];
-    a.TF1 = g->TF[1];
-    a.ctl = g->ctl;
+    a.V0 = ps.V;
+    a.V1 = ps.V2;
+    a.F0 = ps.F[0];
+    a.F1 = ps.F[1];
+    a.F2 = ps.F[2];
+    a.Qpre0 = (E *)ps.Qpre[0];
+    a.Qpre1 = (E *)ps.Qpre[1];
+    a.Qrs0 = (E *)ps.Qrs[0];
+    a.Qrs1 = (E *)ps.Qrs[1];
+    a.TF0 = ps.TF[0];
+    a.TF1 = ps.TF[1];
+    a.ctl = ps.ctl;
     a.seeds = seeds;
     a.ks = ks;
     a.k_all = k_all;
@@ -673,9 +675,9 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
     a.timeout_ns = g->timeout_ns;
     const size_t smem = (2 * ((size_t(1) << tl) + 2) + 3 * (size_t)kStage) * sizeof(E);
     switch (g->tune.block_threads) {
-        case 256: return launch_block<E, 256>(g, a, smem, st);
-        case 1024: return launch_block<E, 1024>(g, a, smem, st);
-        default: return launch_block<E, 512>(g, a, smem, st);
+        case 256: return launch_block<E, 256>(g, a, smem, grid_ctas, st);
+        case 1024: return launch_block<E, 1024>(g, a, smem, grid_ctas, st);
+        default: return launch_block<E, 512>(g, a, smem, grid_ctas, st);
     }
 }
 
@@ -685,10 +687,19 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
                  uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st) {
     if (g->ewidth == 4)
-        return launch_typed<uint32_t>(g, seeds, ks, k_all, nq, out, out_te, stats, per_hop,
-                                      hop_stride, st);
-    return launch_typed<unsigned long long>(g, seeds, ks, k_all, nq, out, out_te, stats, per_hop,
-                                            hop_stride, st);
+        return launch_typed<uint32_t>(g, g->plain, seeds, ks, k_all, nq, out, out_te, stats,
+                                      per_hop, hop_stride, 0, st);
+    return launch_typed<unsigned long long>(g, g->plain, seeds, ks, k_all, nq, out, out_te,
+                                            stats, per_hop, hop_stride, 0, st);
+}
+
+int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
+                       uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st) {
+    if (g->ewidth == 4)
+        return launch_typed<uint32_t>(g, ps, seeds, ks, 0, nq, out, nullptr, nullptr, nullptr, 0,
+                                      grid_ctas, st);
+    return launch_typed<unsigned long long>(g, ps, seeds, ks, 0, nq, out, nullptr, nullptr,
+                                            nullptr, 0, grid_ctas, st);
 }
 
 }  // namespace khop

@@ -46,8 +46,11 @@ struct Request {
     uint64_t t_submit;
 };
 
+constexpr size_t kPlainCohort = 2;   // cohorts this small run on the plain kernel
+
 struct Slot {
     BatchState st;
+    PlainState pst;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     uint32_t *d_lanes = nullptr;
@@ -106,6 +109,7 @@ void post(khop_server *s, const Request &r, uint64_t count, int status) {
 void free_slot(khop_server *s, Slot *sl) {
     if (sl->stream) cudaStreamSynchronize(sl->stream);
     free_batch_state(sl->st);
+    free_plain_state(sl->pst);
     cudaFree(sl->d_lanes);
     cudaFree(sl->d_out);
     cudaFreeHost(sl->h_lanes);
@@ -120,7 +124,7 @@ void free_slot(khop_server *s, Slot *sl) {
 Slot *try_alloc_slot(khop_server *s, GraphCtx *ctx) {
     const uint64_t cap = s->opts.max_batches ? s->opts.max_batches : 8;
     if (ctx->slots.size() >= cap) return nullptr;
-    const uint64_t need = batch_state_bytes(ctx->g) + 4096;
+    const uint64_t need = batch_state_bytes(ctx->g) + plain_state_bytes(ctx->g) + 4096;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return nullptr;
     if ((uint64_t)fr < need + kMarginBytes) return nullptr;
@@ -134,6 +138,11 @@ Slot *try_alloc_slot(khop_server *s, GraphCtx *ctx) {
         std::lock_guard<std::mutex> glk(ctx->g->mu);
         ok = alloc_batch_state(ctx->g, sl->st, &bytes) == KHOP_OK;
         if (ok) ctx->g->device_bytes -= bytes;
+        ok = ok && alloc_plain_state(ctx->g, sl->pst) == KHOP_OK;
+        if (ok) {
+            ctx->g->device_bytes -= sl->pst.bytes;
+            bytes += sl->pst.bytes;
+        }
     }
     ok = ok && cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) == cudaSuccess;
@@ -186,7 +195,13 @@ int launch_cohort(khop_server *s, GraphCtx *ctx, Slot *sl) {
     cudaError_t e = cudaMemcpyAsync(sl->d_lanes, sl->h_lanes, kLaneWords * sizeof(uint32_t),
                                     cudaMemcpyHostToDevice, sl->stream);
     int rc = cuda_status(e);
-    if (rc == KHOP_OK) rc = batch_launch_slot(ctx->g, sl->st, sl->d_lanes, sl->d_out, s->grid_ctas, sl->stream);
+    if (rc == KHOP_OK) {
+        if (c <= kPlainCohort)   // one or two queries: the single-query kernel is cheaper
+            rc = plain_launch_state(ctx->g, sl->pst, sl->d_lanes, sl->d_lanes + 64, c, sl->d_out,
+                                    s->grid_ctas, sl->stream);
+        else
+            rc = batch_launch_slot(ctx->g, sl->st, sl->d_lanes, sl->d_out, s->grid_ctas, sl->stream);
+    }
     if (rc == KHOP_OK)
         rc = cuda_status(cudaMemcpyAsync(sl->h_out, sl->d_out, 64 * sizeof(uint64_t),
                                          cudaMemcpyDeviceToHost, sl->stream));
