@@ -58,6 +58,38 @@ def paper_queries(g, scale_seeds=1.0):
     return np.concatenate(seeds).astype(np.uint32), np.concatenate(ks)
 
 
+KERNEL_SOURCES = {
+    "plain_kernel": ("khop_plain.cu", "khop_internal.cuh"),
+    "batch_kernel": ("khop_batch.cu", "khop_internal.cuh"),
+}
+
+
+def kernel_source_sha(kernel):
+    """sha256 over the source files a kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1905_01294_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on this benchmark's workload, from the
+    committed ncu summary profiles/roofline_traffic.md, or None if the kernel's
+    source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    import re
+    m = re.search(rf"^- {kernel}: dram_bytes_per_launch=(\d+) source_sha256=([0-9a-f]+)", text, re.M)
+    if not m or m.group(2) != kernel_source_sha(kernel):
+        return None
+    return int(m.group(1))
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -265,7 +297,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak):
             "batches_per_step": st["batches"], "rounds_per_step": st["rounds"],
             "pull_rounds_per_step": st["pull_rounds"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": captured_traffic("batch_kernel"),
                          "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"}}
 
 
@@ -468,7 +500,7 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = bytes_sum / t_total / 1e9 * world
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": captured_traffic("plain_kernel"),
                 "kernel": "plain_kernel (persistent push/pull traversal)",
                 "peak_kind": peak_kind}
 
