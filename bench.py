@@ -46,6 +46,24 @@ def workload_graph(scale: int):
     return g, time.time() - t0
 
 
+# The Twitter-shaped power-law graph: Chung-Lu, 41.6M vertices, 1.47e9 distinct
+# directed edges, out/in weights of density ~ w^-2 up to 3e6 (seed 4).
+CHUNGLU = dict(n=41_600_000, edges=1_470_000_000, w_max=3e6, seed=4)
+
+
+def workload(args):
+    """(graph, workload name, batched query count)"""
+    t0 = time.time()
+    if args.workload == "chunglu":
+        g = gen.chunglu(**CHUNGLU)
+        name = (f"chunglu-n41.6M-m{g.nnz}-wmax3e6-seed4 directed plain 300/300/10/10 seeds "
+                f"k=1/2/3/6")
+        return g, name, 1024, time.time() - t0
+    g = gen.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed=1, symmetrize=True)
+    return g, f"kronecker-s{args.scale}-ef16-sym plain 300/300/10/10 seeds k=1/2/3/6", 4096, \
+        time.time() - t0
+
+
 def paper_queries(g, scale_seeds=1.0):
     """300/300/10/10 seeds (seed 2, uniform over out-degree > 0); the first
     300 draws serve k = 1 and 2, the first 10 serve k = 3 and 6."""
@@ -230,11 +248,10 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak):
-    """The batched multi-source form: 4096 seeds (seed 2) with k uniform over
+def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=4096, gname=""):
+    """The batched multi-source form: nq seeds (seed 2) with k uniform over
     {1,2,3,6}, 64 queries per uint64 lane word, one persistent launch per
     step.  Compared with the plain single-query path on the same queries."""
-    nq = 4096
     seeds = gen.seeds(g, nq, seed=2)
     ks = gen.mixed_ks(nq, seed=2)
     d_s = torch.from_numpy(seeds.view(np.int32)).to(dev)
@@ -286,7 +303,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak):
     te = int(kh.as_u64(d_te).sum())
     t = sum(ms) * 1e-3
     achieved = byts / t / 1e9
-    return {"workload": "kronecker-s21-ef16-sym, 4096 seeds (seed 2), k uniform over {1,2,3,6}, "
+    return {"workload": f"{gname}, {nq} seeds (seed 2), k uniform over {{1,2,3,6}}, "
                         "64 queries per uint64 lane word, persistent launch replayed from a "
                         "captured CUDA graph",
             "value": nq * steps / t, "unit": "queries/s", "ms_per_step": float(np.mean(ms)),
@@ -305,17 +322,25 @@ K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
 
 
 def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
-                rates=(25e3, 50e3, 100e3, 200e3, 400e3, 800e3)):
+                rates=(25e3, 50e3, 100e3, 200e3, 400e3, 800e3), G2=None, g2=None, names=""):
     """Open-loop Poisson request stream (seed 3), k from {1:.4, 2:.3, 3:.2,
     6:.1}, uniform seeds over out-degree > 0, served by the continuous-
     batching server; the arrival rate rises until the server saturates.
-    Latency = completion time - scheduled arrival time."""
+    With a second resident graph, a seeded fair coin sends each request to
+    one of the two.  Latency = completion time - scheduled arrival time."""
     plain_rate = 1.0 / sum(p * plain_mean_us_by_k[k] * 1e-6 for k, p in K_MIX)
     points, checked = [], False
     for rate in rates:
         t_arr, ks, sd = gen.poisson_stream(g, nreq, rate, seed=3, k_probs=K_MIX)
+        on2 = np.zeros(nreq, bool)
+        if G2 is not None:
+            on2 = (gen.rand_array(gen.subkey(3, 11), 0, nreq) >> np.uint64(63)).astype(bool)
+            _, _, sd2 = gen.poisson_stream(g2, nreq, rate, seed=5, k_probs=K_MIX)
+            sd = np.where(on2, sd2, sd).astype(np.uint32)
         srv = kh.Server(max_batches=8)
-        srv.submit_many(G, sd[:256], ks[:256])         # warm-up: slots allocated
+        srv.submit_many(G, sd[:256][~on2[:256]], ks[:256][~on2[:256]])   # warm-up: slots allocated
+        if G2 is not None:
+            srv.submit_many(G2, sd[:256][on2[:256]], ks[:256][on2[:256]])
         warm, tw = 0, time.time()
         while warm < 256 and time.time() - tw < 30:
             warm += len(srv.poll_arrays(4096, 100000))
@@ -327,7 +352,16 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
             now = (time.monotonic_ns() - t0) * 1e-9
             j = int(np.searchsorted(t_arr, now, side="right"))
             if j > i:
-                tickets[i:j] = srv.submit_many(G, sd[i:j], ks[i:j])
+                if G2 is None:
+                    tickets[i:j] = srv.submit_many(G, sd[i:j], ks[i:j])
+                else:   # in arrival order, one graph's run at a time
+                    a = i
+                    while a < j:
+                        b = a + 1
+                        while b < j and on2[b] == on2[a]:
+                            b += 1
+                        tickets[a:b] = srv.submit_many(G2 if on2[a] else G, sd[a:b], ks[a:b])
+                        a = b
                 i = j
             done.append(srv.poll_arrays(8192, 0))
         ndone = sum(len(x) for x in done)
@@ -345,7 +379,10 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
         span = (int(res["t_done_ns"].max()) - t0) * 1e-9
         if not checked:
             # each served count equals the same query alone on the plain path
-            alone = kh.as_u64(G.count_mixed(sd, ks, mode=kh.MODE_PLAIN))
+            alone = np.zeros(nreq, np.uint64)
+            alone[~on2] = kh.as_u64(G.count_mixed(sd[~on2], ks[~on2], mode=kh.MODE_PLAIN))
+            if G2 is not None and on2.any():
+                alone[on2] = kh.as_u64(G2.count_mixed(sd[on2], ks[on2], mode=kh.MODE_PLAIN))
             if not np.array_equal(res["count"], alone):
                 raise SystemExit("serving: a served count differs from the query alone")
             checked = True
@@ -354,7 +391,7 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
         if pt["achieved_qps"] < 0.9 * rate:
             break
     best = max(points, key=lambda x: x["achieved_qps"])
-    return {"workload": f"kronecker-s21-ef16-sym resident, open-loop Poisson (seed 3), "
+    return {"workload": f"{names} resident, open-loop Poisson (seed 3), "
                         f"{nreq} requests per rate, k ~ {{1:.4, 2:.3, 3:.2, 6:.1}}",
             "value": best["achieved_qps"], "unit": "queries/s",
             "latency_us_at_best": best["latency_us"],
@@ -370,6 +407,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=21)
+    ap.add_argument("--workload", default="kronecker21", choices=["kronecker21", "chunglu"],
+                    help="kronecker21: the scale-21 Graph500-shaped graph (default); chunglu: "
+                         "the 41.6M-vertex, 1.47e9-edge power-law graph")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="plain path only")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
@@ -395,7 +435,7 @@ def main():
     dev = torch.device("cuda", local)
     kh.lib()
 
-    g, t_gen = workload_graph(args.scale)
+    g, wname, batched_nq, t_gen = workload(args)
     seeds, ks = paper_queries(g)
     nq = seeds.size
     G = kh.Graph.from_csr(g)
@@ -507,10 +547,17 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
-                                        flush, peak)
+                                        flush, peak, nq=batched_nq, gname=wname.split(" ")[0])
         if not args.no_serving:
             mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
-            extras["serving"] = serving_leg(kh, G, g, mean_by_k)
+            if args.workload == "chunglu":
+                g2, _ = workload_graph(21)
+                G2 = kh.Graph.from_csr(g2)
+                extras["serving"] = serving_leg(kh, G, g, mean_by_k, G2=G2, g2=g2,
+                                                names="chunglu-41.6M/1.47e9 and kronecker-s21")
+                G2.close()
+            else:
+                extras["serving"] = serving_leg(kh, G, g, mean_by_k, names=wname.split(" ")[0])
     lat_p = percentiles(lat)
     line = {
         "metric": "k-hop queries/sec (plain sequential, paper protocol)",
@@ -518,7 +565,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": f"kronecker-s{args.scale}-ef16-sym plain 300/300/10/10 seeds k=1/2/3/6",
+        "config": {"workload": wname,
                    "n": g.n, "nnz": g.nnz, "queries_per_step": nq,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single-gpu",

@@ -71,6 +71,15 @@ def _L():
                                                   u64, u64, u64, u64, u32p, u32p, ctypes.c_int]
             lib.khopgen_poisson.argtypes = [u64, ctypes.c_double, u64, ctypes.c_void_p, u32p,
                                             ctypes.c_int, u64, u32p, ctypes.c_void_p, u32p, u32p]
+            lib.khopgen_powerlaw_weights.restype = ctypes.c_double
+            lib.khopgen_powerlaw_weights.argtypes = [u64, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_void_p]
+            lib.khopgen_chunglu_begin.restype = i64
+            lib.khopgen_chunglu_begin.argtypes = [u64, ctypes.c_void_p, u32p, ctypes.c_void_p,
+                                                  u32p, u64, u64, u64, u64, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_uint64),
+                                                  ctypes.POINTER(ctypes.c_void_p)]
+            lib.khopgen_chunglu_finish.argtypes = [ctypes.c_void_p, u64p, u32p]
             _lib = lib
     return _lib
 
@@ -194,6 +203,68 @@ def rmat_edges_unpermuted(scale: int, m: int, A=0.57, B=0.19, C=0.19, seed: int 
     if rc != 0:
         raise ValueError("bad R-MAT parameters")
     return src, dst
+
+
+def powerlaw_weights(n: int, w_max: float, total: float) -> tuple[np.ndarray, float]:
+    """Quantile weights of the density p(w) ~ w^-2 on [w_min, w_max]:
+    w(i) = w_min / (1 - u_i (1 - w_min / w_max)), u_i = (i + 1/2) / n, with
+    w_min chosen (bisection) so that the weights sum to `total`."""
+    w = np.empty(n, dtype=np.float64)
+    w_min = _L().khopgen_powerlaw_weights(n, float(w_max), float(total), _p(w))
+    if w_min < 0:
+        raise ValueError("no w_min gives that total")
+    return w, w_min
+
+
+def alias_table(w: np.ndarray):
+    """Walker alias table (prob, alias) for weights w."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    prob = np.empty(w.size, dtype=np.float64)
+    alias = np.empty(w.size, dtype=np.uint32)
+    if _L().khopgen_alias_build(w.size, _p(w), _p(prob), _p(alias)) != 0:
+        raise ValueError("bad weights")
+    return prob, alias
+
+
+def chunglu(n: int, edges: int, w_max: float, seed: int = 4, nthreads: int = 0,
+            overdraw: float = 1.12) -> CSRGraph:
+    """Directed Chung-Lu graph shaped like a social follow graph.
+
+    Out- and in-weights are the power-law quantile weights of powerlaw_weights
+    (summing to `edges`), each assigned to the vertices by its own seeded
+    permutation.  Candidate edge i has tail ~ w_out and head ~ w_in (alias
+    tables, draw i of two counter-based streams); self-loops are dropped and
+    duplicates collapsed.  The graph keeps the distinct edges whose first
+    occurrence lies in the shortest prefix of candidates -- a multiple of 2^20
+    -- that yields at least `edges` distinct edges.  Rows are sorted."""
+    w, w_min = powerlaw_weights(n, w_max, edges)
+    w_out = np.empty(n, np.float64)
+    w_in = np.empty(n, np.float64)
+    w_out[permutation(n, subkey(seed, _SUB_WPERM_OUT))] = w
+    w_in[permutation(n, subkey(seed, _SUB_WPERM_IN))] = w
+    del w
+    po, ao = alias_table(w_out)
+    pi, ai = alias_table(w_in)
+    del w_out, w_in
+    m = -(-int(edges * overdraw) // (1 << 20)) << 20
+    while True:
+        h = ctypes.c_void_p()
+        mstar = ctypes.c_uint64()
+        kept = _L().khopgen_chunglu_begin(n, _p(po), _p(ao), _p(pi), _p(ai),
+                                          subkey(seed, _SUB_SRC), subkey(seed, _SUB_DST), m,
+                                          edges, nthreads, ctypes.byref(mstar), ctypes.byref(h))
+        if kept == -2:
+            m = -(-int(m * 1.1) // (1 << 20)) << 20
+            continue
+        if kept < 0:
+            raise MemoryError("Chung-Lu build failed")
+        break
+    row_ptr = np.empty(n + 1, dtype=np.uint64)
+    col = np.empty(max(kept, 1), dtype=np.uint32)
+    _L().khopgen_chunglu_finish(h, _p(row_ptr), _p(col))
+    params = dict(kind="chunglu", n=n, edges_target=edges, w_max=w_max, w_min=w_min, seed=seed,
+                  candidates_drawn=m, prefix_kept=int(mstar.value), edges=int(kept))
+    return CSRGraph(n, row_ptr, col[:kept], False, f"chunglu-n{n}-m{edges}-seed{seed}", params)
 
 
 def permutation(n: int, key: int) -> np.ndarray:

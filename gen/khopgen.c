@@ -323,9 +323,10 @@ typedef struct {
 } cl_ctx;
 
 static inline uint32_t alias_pick(uint64_t r, uint64_t n, const double *prob, const uint32_t *alias) {
-    /* high bits pick the column, low 53 bits decide column vs alias */
-    uint64_t col = (uint64_t)(((__uint128_t)r * n) >> 64);
-    double u = (double)(r & ((1ULL << 53) - 1)) * 0x1.0p-53;
+    /* disjoint halves of the draw: the high 32 bits pick the column (n < 2^32),
+       the low 32 bits decide column vs alias */
+    const uint64_t col = ((r >> 32) * n) >> 32;
+    const double u = (double)(r & 0xffffffffULL) * 0x1.0p-32;
     return u < prob[col] ? (uint32_t)col : alias[col];
 }
 
@@ -372,4 +373,210 @@ void khopgen_poisson(uint64_t count, double lam, uint64_t key,
         if (idx >= n_eligible) idx = n_eligible - 1;
         seeds[i] = eligible[idx];
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Power-law weights: w(i) = w_min / (1 - u_i (1 - w_min / w_max)),     */
+/* u_i = (i + 1/2) / n -- the quantiles of the density p(w) ~ w^-2 on   */
+/* [w_min, w_max] -- with w_min found by bisection so that the weights  */
+/* sum to `total`.  Returns w_min (or -1 if no w_min fits).             */
+static double pl_sum(uint64_t n, double w_min, double w_max) {
+    double s = 0, c = 0;   /* Kahan summation */
+    const double r = 1.0 - w_min / w_max;
+    for (uint64_t i = 0; i < n; ++i) {
+        const double u = ((double)i + 0.5) / (double)n;
+        const double y = w_min / (1.0 - u * r) - c;
+        const double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    return s;
+}
+
+double khopgen_powerlaw_weights(uint64_t n, double w_max, double total, double *w) {
+    double lo = 1e-9, hi = w_max;
+    if (pl_sum(n, hi, w_max) < total || pl_sum(n, lo, w_max) > total) return -1.0;
+    for (int it = 0; it < 100 && hi - lo > 1e-12 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (pl_sum(n, mid, w_max) < total) lo = mid; else hi = mid;
+    }
+    const double w_min = 0.5 * (lo + hi);
+    const double r = 1.0 - w_min / w_max;
+    for (uint64_t i = 0; i < n; ++i) w[i] = w_min / (1.0 - (((double)i + 0.5) / (double)n) * r);
+    return w_min;
+}
+
+/* ------------------------------------------------------------------ */
+/* Chung-Lu graph with an exact-prefix dedup.  Candidates i = 0..m-1   */
+/* are drawn (src ~ alias_out, dst ~ alias_in); self-loops dropped.    */
+/* Each distinct edge keeps its first occurrence i.  The output is the */
+/* set of distinct edges whose first occurrence is below M*, where M*  */
+/* is the smallest multiple of 2^20 for which that set reaches         */
+/* `target` edges (so the result is `target` edges plus less than one  */
+/* 2^20 block's new edges).  Rows come out sorted.                     */
+typedef struct {
+    uint64_t n, m;
+    const double *po, *pi; const uint32_t *ao, *ai;
+    uint64_t ks, kd;
+    uint32_t *src, *dst;
+    uint64_t *deg, *off;        /* counts / cursors, offsets [n+1] */
+    uint64_t *pair;             /* (dst << 32 | first index) per row */
+    uint64_t *udeg;             /* unique entries per row */
+    uint64_t *hist;             /* [nthreads][nblk] first-occurrence block histogram */
+    uint64_t nblk; int nthreads;
+    uint64_t mstar;             /* cut: keep first occurrence < mstar */
+    uint64_t *kdeg;             /* kept entries per row */
+    uint64_t *row_ptr; uint32_t *col;
+    uint64_t next_row;          /* dynamic row scheduling */
+} cl_build;
+
+static void clb_gen(void *vc, uint64_t lo, uint64_t hi) {
+    cl_build *c = (cl_build *)vc;
+    uint64_t bs = mix64(c->ks), bd = mix64(c->kd);
+    for (uint64_t i = lo; i < hi; ++i) {
+        c->src[i] = alias_pick(mix64(bs + (i + 1) * GAMMA), c->n, c->po, c->ao);
+        c->dst[i] = alias_pick(mix64(bd + (i + 1) * GAMMA), c->n, c->pi, c->ai);
+    }
+}
+
+static void clb_count(void *vc, uint64_t lo, uint64_t hi) {
+    cl_build *c = (cl_build *)vc;
+    for (uint64_t i = lo; i < hi; ++i)
+        if (c->src[i] != c->dst[i]) __atomic_fetch_add(&c->deg[c->src[i]], 1, __ATOMIC_RELAXED);
+}
+
+static void clb_scatter(void *vc, uint64_t lo, uint64_t hi) {
+    cl_build *c = (cl_build *)vc;
+    for (uint64_t i = lo; i < hi; ++i) {
+        const uint32_t s = c->src[i], d = c->dst[i];
+        if (s == d) continue;
+        const uint64_t p = __atomic_fetch_add(&c->deg[s], 1, __ATOMIC_RELAXED);
+        c->pair[p] = ((uint64_t)d << 32) | (uint64_t)(uint32_t)i;
+    }
+}
+
+static int cmp_u64(const void *x, const void *y) {
+    uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* rows: sort pairs, keep the first occurrence of each dst, count per block */
+typedef struct { cl_build *c; int tid; } clb_arg;
+static void *clb_rows(void *va) {
+    clb_arg *A = (clb_arg *)va;
+    cl_build *c = A->c;
+    uint64_t *h = c->hist + (uint64_t)A->tid * c->nblk;
+    for (;;) {
+        uint64_t lo = __atomic_fetch_add(&c->next_row, 1024, __ATOMIC_RELAXED);
+        if (lo >= c->n) break;
+        uint64_t hi = lo + 1024 < c->n ? lo + 1024 : c->n;
+        for (uint64_t r = lo; r < hi; ++r) {
+            uint64_t *x = c->pair + c->off[r];
+            const uint64_t d = c->off[r + 1] - c->off[r];
+            if (d > 1) qsort(x, d, sizeof(uint64_t), cmp_u64);
+            uint64_t u = 0;
+            for (uint64_t j = 0; j < d; ++j)
+                if (u == 0 || (x[j] >> 32) != (x[u - 1] >> 32)) x[u++] = x[j];   /* min index first */
+            c->udeg[r] = u;
+            for (uint64_t j = 0; j < u; ++j) h[(x[j] & 0xffffffffULL) >> 20]++;
+        }
+    }
+    return NULL;
+}
+
+static void clb_keep(void *vc, uint64_t lo, uint64_t hi) {
+    cl_build *c = (cl_build *)vc;
+    for (uint64_t r = lo; r < hi; ++r) {
+        uint64_t *x = c->pair + c->off[r];
+        uint64_t k = 0;
+        for (uint64_t j = 0; j < c->udeg[r]; ++j)
+            if ((x[j] & 0xffffffffULL) < c->mstar) x[k++] = x[j];
+        c->kdeg[r] = k;
+    }
+}
+
+static void clb_copy(void *vc, uint64_t lo, uint64_t hi) {
+    cl_build *c = (cl_build *)vc;
+    for (uint64_t r = lo; r < hi; ++r) {
+        const uint64_t *x = c->pair + c->off[r];
+        uint32_t *o = c->col + c->row_ptr[r];
+        for (uint64_t j = 0; j < c->kdeg[r]; ++j) o[j] = (uint32_t)(x[j] >> 32);
+    }
+}
+
+/* Returns the number of edges kept (>= target), or -1 (memory / m too
+ * large for 32-bit indices), or -2 (m candidates give fewer than target
+ * distinct edges: call again with a larger m).  *mstar_out = M*. */
+int64_t khopgen_chunglu_begin(uint64_t n, const double *prob_out, const uint32_t *alias_out,
+                              const double *prob_in, const uint32_t *alias_in,
+                              uint64_t key_src, uint64_t key_dst, uint64_t m, uint64_t target,
+                              int nthreads, uint64_t *mstar_out, void **handle) {
+    if (m >= (1ULL << 32)) return -1;
+    nthreads = default_threads(nthreads);
+    cl_build *c = (cl_build *)calloc(1, sizeof(cl_build));
+    if (!c) return -1;
+    c->n = n; c->m = m; c->po = prob_out; c->pi = prob_in; c->ao = alias_out; c->ai = alias_in;
+    c->ks = key_src; c->kd = key_dst; c->nthreads = nthreads;
+    c->nblk = (m >> 20) + 1;
+    c->src = (uint32_t *)malloc(m * sizeof(uint32_t));
+    c->dst = (uint32_t *)malloc(m * sizeof(uint32_t));
+    c->deg = (uint64_t *)calloc(n + 1, sizeof(uint64_t));
+    c->off = (uint64_t *)malloc((n + 1) * sizeof(uint64_t));
+    c->udeg = (uint64_t *)malloc(n * sizeof(uint64_t));
+    c->kdeg = (uint64_t *)malloc(n * sizeof(uint64_t));
+    c->hist = (uint64_t *)calloc((uint64_t)nthreads * c->nblk, sizeof(uint64_t));
+    if (!c->src || !c->dst || !c->deg || !c->off || !c->udeg || !c->kdeg || !c->hist) goto fail;
+    pfor(clb_gen, c, m, 1u << 20, nthreads);
+    pfor(clb_count, c, m, 1u << 20, nthreads);
+    uint64_t acc = 0;
+    for (uint64_t v = 0; v < n; ++v) { c->off[v] = acc; acc += c->deg[v]; c->deg[v] = c->off[v]; }
+    c->off[n] = acc;
+    c->pair = (uint64_t *)malloc((acc ? acc : 1) * sizeof(uint64_t));
+    if (!c->pair) goto fail;
+    pfor(clb_scatter, c, m, 1u << 20, nthreads);
+    free(c->src); c->src = NULL;
+    free(c->dst); c->dst = NULL;
+    {
+        pthread_t th[64];
+        clb_arg args[64];
+        int started = 0;
+        for (int t = 0; t < nthreads && t < 64; ++t) {
+            args[t].c = c; args[t].tid = t;
+            if (t == 0) continue;
+            if (pthread_create(&th[started], NULL, clb_rows, &args[t]) == 0) ++started;
+            else args[t].tid = -1;
+        }
+        clb_rows(&args[0]);
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    }
+    /* smallest block boundary reaching the target */
+    uint64_t cum = 0, blk = 0;
+    for (; blk < c->nblk; ++blk) {
+        for (int t = 0; t < nthreads; ++t) cum += c->hist[(uint64_t)t * c->nblk + blk];
+        if (cum >= target) break;
+    }
+    if (cum < target) {
+        /* free everything; the caller retries with more candidates */
+        free(c->deg); free(c->off); free(c->udeg); free(c->kdeg); free(c->hist); free(c->pair); free(c);
+        return -2;
+    }
+    c->mstar = (blk + 1) << 20;
+    pfor(clb_keep, c, n, 4096, nthreads);
+    *mstar_out = c->mstar;
+    *handle = c;
+    return (int64_t)cum;
+fail:
+    free(c->src); free(c->dst); free(c->deg); free(c->off); free(c->udeg); free(c->kdeg);
+    free(c->hist); free(c->pair); free(c);
+    return -1;
+}
+
+void khopgen_chunglu_finish(void *handle, uint64_t *row_ptr, uint32_t *col) {
+    cl_build *c = (cl_build *)handle;
+    uint64_t acc = 0;
+    for (uint64_t v = 0; v < c->n; ++v) { row_ptr[v] = acc; acc += c->kdeg[v]; }
+    row_ptr[c->n] = acc;
+    c->row_ptr = row_ptr; c->col = col;
+    pfor(clb_copy, c, c->n, 4096, c->nthreads);
+    free(c->deg); free(c->off); free(c->udeg); free(c->kdeg); free(c->hist); free(c->pair); free(c);
 }

@@ -98,3 +98,42 @@ def test_poisson_stream_shape():
 def test_mixed_ks():
     ks = gen.mixed_ks(4096, seed=2)
     assert set(np.unique(ks).tolist()) == {1, 2, 3, 6}
+
+
+def test_powerlaw_weights_are_the_quantiles_and_sum_to_the_total():
+    w, w_min = gen.powerlaw_weights(100000, 5000.0, 1e6)
+    assert abs(w.sum() - 1e6) < 1e-3
+    assert (np.diff(w) > 0).all() and w[0] > w_min and w[-1] < 5000.0
+    # the fraction of weights above x follows the density p(w) ~ w^-2:
+    # P(W > x) = (1/x - 1/w_max) / (1/w_min - 1/w_max)
+    for x in (2 * w_min, 10 * w_min, 100 * w_min):
+        want = (1 / x - 1 / 5000.0) / (1 / w_min - 1 / 5000.0)
+        assert abs(np.mean(w > x) - want) < 2e-4
+
+
+def test_alias_sampler_matches_the_weights():
+    n, m = 1000, 2_000_000
+    w = np.arange(1, n + 1, dtype=np.float64) ** 1.5
+    po, ao = gen.alias_table(w)
+    src = np.empty(m, np.uint32)
+    dst = np.empty(m, np.uint32)
+    gen._L().khopgen_chunglu_edges(n, gen._p(po), gen._p(ao), gen._p(po), gen._p(ao), 5, 6, 0, m,
+                                   gen._p(src), gen._p(dst), 0)
+    for x in (src, dst):
+        c = np.bincount(x, minlength=n)
+        e = m * w / w.sum()
+        z = (c - e) / np.sqrt(e)
+        assert np.abs(z).max() < 5.5 and abs(np.mean(z ** 2) - 1) < 0.15
+
+
+def test_chunglu_graph_valid_deterministic_and_sized():
+    g = gen.chunglu(50000, 600000, 3000.0, seed=4)
+    _check_csr(g, False)
+    assert 600000 <= g.nnz < 600000 + (1 << 20)
+    g2 = gen.chunglu(50000, 600000, 3000.0, seed=4, nthreads=3)
+    np.testing.assert_array_equal(g.col_idx, g2.col_idx)
+    np.testing.assert_array_equal(g.row_ptr, g2.row_ptr)
+    outd = np.diff(g.row_ptr).astype(np.int64)
+    ind = np.bincount(g.col_idx, minlength=g.n)
+    assert 0.5 * 3000 < outd.max() < 3000 * 1.3 and 0.5 * 3000 < ind.max() < 3000 * 1.3
+    assert np.corrcoef(outd, ind)[0, 1] < 0.1      # independent out/in weights
