@@ -227,7 +227,7 @@ def alias_table(w: np.ndarray):
 
 
 def chunglu(n: int, edges: int, w_max: float, seed: int = 4, nthreads: int = 0,
-            overdraw: float = 1.12) -> CSRGraph:
+            overdraw: float = 1.25) -> CSRGraph:
     """Directed Chung-Lu graph shaped like a social follow graph.
 
     Out- and in-weights are the power-law quantile weights of powerlaw_weights
