@@ -108,6 +108,18 @@ def captured_traffic(kernel):
     return int(m.group(1))
 
 
+def over_ranks(dist, t_local, queries_local, device):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (MAX) and every rank's queries (SUM).  Returns (t_max, queries, qps)."""
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    q = torch.tensor([float(queries_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(q, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(q.item()), float(q.item()) / float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -500,16 +512,10 @@ def main():
             raise SystemExit("counts changed between steps")
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_total = sum(step_ms) * 1e-3
+    t_total, queries_total, value = over_ranks(dist, sum(step_ms) * 1e-3, nq * args.steps, dev)
     if dist is not None:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-
-    queries_total = nq * args.steps * world
-    value = queries_total / t_total
     gteps = te_sum * world / t_total / 1e9
 
     # e2e: public API, pinned host inputs, counts back to the host, per step
@@ -533,12 +539,13 @@ def main():
         e_t += time.perf_counter() - t0
         if not np.array_equal(h_out.numpy().view(np.uint64), ref_counts):
             raise SystemExit("e2e counts differ")
-    e2e = {"value": nq * args.steps * world / e_t, "unit": "queries/s",
+    _, _, e2e_qps = over_ranks(dist, e_t, nq * args.steps, dev)
+    e2e = {"value": e2e_qps, "unit": "queries/s",
            "h2d_bytes_per_step": int(seeds.nbytes + ks.nbytes),
            "d2h_bytes_per_step": int(nq * 8)}
 
     peak, peak_kind = load_peaks()
-    achieved = bytes_sum / t_total / 1e9 * world
+    achieved = bytes_sum / t_total / 1e9   # per GPU: one rank's kernel bytes over the max time
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": captured_traffic("plain_kernel"),
                 "kernel": "plain_kernel (persistent push/pull traversal)",
