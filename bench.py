@@ -452,8 +452,8 @@ def main():
     nq = seeds.size
     G = kh.Graph.from_csr(g)
     if not args.case:
-        tune_seeds = gen.seeds(g, 64, seed=9)   # tuning seeds differ from the measured ones
-        t = G.autotune(tune_seeds, 6)
+        # tuning sample: 1024 seeds (seed 9, not the measured ones), k mixed over {1,2,3,6}
+        t = G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
         tuning = {f: (getattr(t, f) if isinstance(getattr(t, f), int) else round(getattr(t, f), 3))
                   for f, _ in t._fields_}
     if args.case:

@@ -133,12 +133,15 @@ int khop_graph_get_tuning(const khop_graph *g, khop_tuning *t);
 int khop_graph_set_tuning(khop_graph *g, const khop_tuning *t);
 
 /*
- * Pick tuning values for this graph by timing candidate settings on `nq`
- * seeds (device array `seeds`, k = `k`), keeping the fastest, and apply them.
- * Synchronises `stream`.  Never changes a count.
+ * Pick tuning values for this graph by timing candidate settings -- grid
+ * shape, push tile, alpha and beta of the plain path, then alpha and beta of
+ * the batched path -- on `nq` queries (device array `seeds`; per-seed hops in
+ * the device array `ks`, or, if ks is NULL, `k` for every seed), keeping the
+ * fastest of each, and apply them.  Synchronises `stream`.  Never changes a
+ * count.
  */
-int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, uint32_t k,
-                  void *stream, khop_tuning *chosen);
+int khop_autotune(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
+                  uint32_t k, void *stream, khop_tuning *chosen);
 
 /* ---- counting ---------------------------------------------------------- */
 /*

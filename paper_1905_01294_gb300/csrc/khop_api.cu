@@ -83,17 +83,17 @@ int khop_batch_stats(khop_graph *g, uint64_t *batches, uint64_t *bytes, uint64_t
 
 // ---------------------------------------------------------------------------
 // Autotuner: coordinate descent over the tunables, each candidate timed with
-// CUDA events (best of two runs) on the caller's seeds; counts never depend
+// CUDA events (best of three runs) on the caller's seeds; counts never depend
 // on the tuning, so only the time decides.
 
 namespace {
 
-float time_plain(khop_graph *g, const uint32_t *seeds, uint64_t nq, uint32_t k, uint64_t *out,
-                 cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int *rc) {
+float time_plain(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
+                 uint64_t *out, cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int *rc) {
     float best = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(a, st);
-        *rc = plain_launch(g, seeds, nullptr, k, nq, out, nullptr, nullptr, nullptr, 0, st);
+        *rc = plain_launch(g, seeds, ks, 0, nq, out, nullptr, nullptr, nullptr, 0, st);
         cudaEventRecord(b, st);
         if (*rc != KHOP_OK || cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
         float ms = 0;
@@ -106,7 +106,7 @@ float time_plain(khop_graph *g, const uint32_t *seeds, uint64_t nq, uint32_t k, 
 float time_batch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int *rc) {
     float best = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(a, st);
         *rc = batch_launch(g, seeds, ks, nq, out, st);
         cudaEventRecord(b, st);
@@ -120,9 +120,9 @@ float time_batch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
 
 }  // namespace
 
-extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, uint32_t k,
-                             void *stream, khop_tuning *chosen) {
-    if (!g || !seeds || nq == 0 || k == 0) return KHOP_EINVAL;
+extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, const uint32_t *ks_in,
+                             uint64_t nq, uint32_t k, void *stream, khop_tuning *chosen) {
+    if (!g || !seeds || nq == 0 || (!ks_in && k == 0)) return KHOP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = order_after_previous(g, st);
@@ -137,8 +137,12 @@ extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, 
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e == cudaSuccess) {
-        std::vector<uint32_t> hk(nq, k);
-        e = cudaMemcpyAsync(ks, hk.data(), nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        if (ks_in) {
+            e = cudaMemcpyAsync(ks, ks_in, nq * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+        } else {
+            std::vector<uint32_t> hk(nq, k);
+            e = cudaMemcpyAsync(ks, hk.data(), nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e != cudaSuccess) {
@@ -154,12 +158,12 @@ extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, 
     // plain path: grid shape, push tile, alpha, beta
     struct Shape { int block, per_sm; };
     const Shape shapes[] = {{512, 2}, {1024, 1}, {256, 4}, {512, 1}};
-    float best = time_plain(g, seeds, nq, k, out, st, a, b, &rc);
+    float best = time_plain(g, seeds, ks, nq, out, st, a, b, &rc);
     Shape bs{t.block_threads, t.blocks_per_sm};
     for (const Shape &s : shapes) {
         t.block_threads = s.block;
         t.blocks_per_sm = s.per_sm;
-        const float ms = time_plain(g, seeds, nq, k, out, st, a, b, &rc);
+        const float ms = time_plain(g, seeds, ks, nq, out, st, a, b, &rc);
         if (ms < best) { best = ms; bs = s; }
     }
     t.block_threads = bs.block;
@@ -167,21 +171,21 @@ extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, uint64_t nq, 
     int best_tile = t.push_tile;
     for (int tile : {512, 1024, 2048, 4096}) {
         t.push_tile = tile;
-        const float ms = time_plain(g, seeds, nq, k, out, st, a, b, &rc);
+        const float ms = time_plain(g, seeds, ks, nq, out, st, a, b, &rc);
         if (ms < best) { best = ms; best_tile = tile; }
     }
     t.push_tile = best_tile;
     float best_alpha = t.alpha;
     for (float al : {4.0f, 8.0f, 14.0f, 24.0f, 40.0f}) {
         t.alpha = al;
-        const float ms = time_plain(g, seeds, nq, k, out, st, a, b, &rc);
+        const float ms = time_plain(g, seeds, ks, nq, out, st, a, b, &rc);
         if (ms < best) { best = ms; best_alpha = al; }
     }
     t.alpha = best_alpha;
     float best_beta = t.beta;
     for (float be : {8.0f, 24.0f, 64.0f}) {
         t.beta = be;
-        const float ms = time_plain(g, seeds, nq, k, out, st, a, b, &rc);
+        const float ms = time_plain(g, seeds, ks, nq, out, st, a, b, &rc);
         if (ms < best) { best = ms; best_beta = be; }
     }
     t.beta = best_beta;

@@ -83,9 +83,9 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // the other G - 1 CTAs add 1 -- so the barrier's additions total exactly 2^31:
 // the top bit flips when, and only when, the last CTA has arrived, and the low
 // bits return to where they were (no reset is ever needed).  After a CTA-wide
-// __syncthreads, thread 0 publishes the CTA's writes with a gpu-scope acq_rel
-// fence and its atomic arrival, then polls the word with acquire loads until
-// the top bit differs from the value its own atomic returned.  The wait is
+// __syncthreads, thread 0 publishes the CTA's writes with a gpu-scope release
+// atomic arrival, then polls the word with acquire loads until the top bit
+// differs from the value its own atomic returned.  The wait is
 // bounded by `timeout_ns` of %globaltimer and by an iteration cap; on expiry
 // (or if another CTA already flagged a timeout) it sets KHOP_DEVERR_TIMEOUT in
 // *err and returns false, and the caller leaves the kernel.
@@ -100,8 +100,9 @@ __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, in
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        fence_acq_rel_gpu();
-        const unsigned old = atomicAdd(&bw->count, add);
+        unsigned old;   // the arrival is a release: the CTA's writes precede it
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
+                     : "=r"(old) : "l"(&bw->count), "r"(add) : "memory");
         const uint64_t t0 = globaltimer_ns();
         uint64_t spins = 0;
         while (((ld_acquire_u32(&bw->count) ^ old) & 0x80000000u) == 0u) {

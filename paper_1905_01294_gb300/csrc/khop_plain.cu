@@ -24,6 +24,7 @@ namespace {
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 
 constexpr int kPushUnroll = 4;   // edges in flight per thread in a push tile
+constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big read V before test-and-set
 constexpr int kPullWords = 4;    // bitmap words a warp works on at once in a pull round
 constexpr int kFlatILP = 4;      // in-edges per lane per step of the flattened pull scan
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
@@ -72,7 +73,9 @@ __device__ __forceinline__ T sel3(T x0, T x1, T x2, unsigned i) {
 template <typename E>
 struct Round {
     bool first, last;
+    bool precheck;           // load the visited word before the test-and-set (big rounds)
     uint32_t seed;
+    E seed_rs;               // row start of the seed (round 1)
     uint32_t *V;             // visited bitmap of this query
     const uint32_t *Fin;
     uint32_t *Fout;
@@ -231,7 +234,7 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
         if (R.first) {
             if (threadIdx.x == 0) {
                 s_pre[0] = (E)0;
-                s_rs[0] = a.rp[R.seed];
+                s_rs[0] = R.seed_rs;
             }
             nitems = 1;
         } else {
@@ -268,7 +271,7 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
                 bool disc = false;
                 if (ok[u]) {
                     const uint32_t wi = w[u] >> 5, bit = 1u << (w[u] & 31);
-                    if (!(R.V[wi] & bit)) disc = !(atomicOr(&R.V[wi], bit) & bit);
+                    if (!R.precheck || !(R.V[wi] & bit)) disc = !(atomicOr(&R.V[wi], bit) & bit);
                 }
                 E rs = 0, d = 0;
                 if (disc && !R.last) {
@@ -407,16 +410,30 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
     if (lane == 0 && scanned) atomicAdd(&sh.scan, (unsigned long long)scanned);
 }
 
+// A query that needs a traversal: its seed, k and seed row.
+template <typename E>
+struct QueryHead {
+    uint32_t s, k;
+    E rs, re;
+};
+
 // Answer the queries that need no traversal -- k = 0, a seed >= n, or a seed
 // without out-edges (count 0 and TE 0) -- and return the index of the next
-// query that does.  Only thread 0 of CTA 0 writes (when `write` is set).
+// query that does, with its head in *h.  Only thread 0 of CTA 0 writes (when
+// `write` is set).
 template <typename E>
 __device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t q, bool write,
-                                                 uint64_t &t_prev) {
+                                                 uint64_t &t_prev, QueryHead<E> *h) {
     for (; q < a.nq; ++q) {
         const uint32_t s = a.seeds[q];
         const uint32_t k = a.ks ? a.ks[q] : a.k_all;
-        if (s < a.n && k > 0 && a.rp[s + 1] > a.rp[s]) break;
+        if (s < a.n && k > 0) {
+            const E rs = a.rp[s], re = a.rp[s + 1];
+            if (re > rs) {
+                if (h) *h = QueryHead<E>{s, k, rs, re};
+                break;
+            }
+        }
         if (write) {
             const bool bad = s >= a.n;
             const uint64_t now = globaltimer_ns();
@@ -440,15 +457,10 @@ __device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t
 // can reach them, so marking them spares the pull sweeps) plus the seed of
 // query q.  Grid-stride over the words.
 template <typename E>
-__device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V, uint64_t q,
-                                             uint64_t gtid, uint64_t gthreads) {
-    uint64_t sw = ~0ull;
-    uint32_t sb = 0;
-    if (q < a.nq) {
-        const uint32_t s = a.seeds[q];
-        sw = s >> 5;
-        sb = 1u << (s & 31);
-    }
+__device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V, bool any,
+                                             uint32_t seed, uint64_t gtid, uint64_t gthreads) {
+    const uint64_t sw = any ? (uint64_t)(seed >> 5) : ~0ull;
+    const uint32_t sb = 1u << (seed & 31);
     for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = a.noin[i] | (i == sw ? sb : 0u);
 }
 
@@ -479,23 +491,24 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     unsigned long long *slots = (unsigned long long *)a.ctl->slot;
 
     // Launch prologue: frontier bitmaps zero, V0 = noin | {first seed}.
-    uint64_t q = skip_trivial(a, 0, b0, t_prev);
+    QueryHead<E> cur{0u, 0u, (E)0, (E)0}, nxt{0u, 0u, (E)0, (E)0};
+    uint64_t q = skip_trivial(a, 0, b0, t_prev, &cur);
     for (uint64_t i = gtid; i < a.nw; i += gthreads) {
         a.F0[i] = 0u;
         a.F1[i] = 0u;
         a.F2[i] = 0u;
     }
-    prep_visited(a, a.V0, q, gtid, gthreads);
+    prep_visited(a, a.V0, q < a.nq, cur.s, gtid, gthreads);
     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
 
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
     unsigned par = 0;     // which visited bitmap the current query uses
     while (q < a.nq) {
-        const uint32_t s = a.seeds[q];
-        const uint32_t k = a.ks ? a.ks[q] : a.k_all;
+        const uint32_t s = cur.s;
+        const uint32_t k = cur.k;
         uint32_t *V = par ? a.V1 : a.V0;
         uint32_t *Vnext = par ? a.V0 : a.V1;
-        const uint64_t qn = skip_trivial(a, q + 1, false, t_prev);   // next query (no writes)
+        const uint64_t qn = skip_trivial(a, q + 1, false, t_prev, &nxt);   // next query (no writes)
         if (all_pull) {
             // Round 1 pulls from the bitmap {s}: set it up before the round.
             uint32_t *Fs = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
@@ -504,7 +517,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns))
                 return;
         }
-        uint64_t mf = (uint64_t)(a.rp[s + 1] - a.rp[s]);   // out-edges of the frontier {s}
+        uint64_t mf = (uint64_t)(cur.re - cur.rs);   // out-edges of the frontier {s}
         uint64_t items = 1;
         uint64_t nf = 1;
         uint64_t count = 0, te = 0, bytes = 0, sum_mf = 0, visited = 1;
@@ -531,7 +544,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             // also prepare the next query's visited bitmap.
             uint32_t *Fz = sel3(a.F0, a.F1, a.F2, izero);
             for (uint64_t i = gtid; i < a.nw; i += gthreads) Fz[i] = 0u;
-            if (r == 1) prep_visited(a, Vnext, qn, gtid, gthreads);
+            if (r == 1) prep_visited(a, Vnext, qn < a.nq, nxt.s, gtid, gthreads);
             if (b0) {
                 slots[kSlotWords * izero + 0] = 0ull;
                 slots[kSlotWords * izero + 1] = 0ull;
@@ -543,7 +556,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             Round<E> R;
             R.first = r == 1;
             R.last = r == k;
+            R.precheck = mf > kPrecheckEdges;
             R.seed = s;
+            R.seed_rs = cur.rs;
             R.V = V;
             R.Fin = sel3(a.F0, a.F1, a.F2, iin);
             R.Fout = sel3(a.F0, a.F1, a.F2, iout);
@@ -601,9 +616,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                     a.per_hop[q * a.hop_stride + r] = 0ull;
             }
             t_prev = now;
-            skip_trivial(a, q + 1, true, t_prev);   // answer the trivial queries up to qn
+            skip_trivial(a, q + 1, true, t_prev, (QueryHead<E> *)nullptr);   // answer the trivial queries up to qn
         }
         q = qn;
+        cur = nxt;
         par ^= 1u;
     }
 }

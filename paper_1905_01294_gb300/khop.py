@@ -100,7 +100,7 @@ def lib():
                 "khop_graph_device_bytes": (i32, [vp, ctypes.POINTER(u64)]),
                 "khop_graph_get_tuning": (i32, [vp, ctypes.POINTER(khop_tuning)]),
                 "khop_graph_set_tuning": (i32, [vp, ctypes.POINTER(khop_tuning)]),
-                "khop_autotune": (i32, [vp, vp, u64, u32, vp, ctypes.POINTER(khop_tuning)]),
+                "khop_autotune": (i32, [vp, vp, vp, u64, u32, vp, ctypes.POINTER(khop_tuning)]),
                 "khop_count": (i32, [vp, vp, u64, u32, vp, vp]),
                 "khop_count_mixed": (i32, [vp, vp, vp, u64, vp, i32, vp]),
                 "khop_count_ex": (i32, [vp, vp, vp, u64, vp, vp, vp, vp, u32, vp]),
@@ -175,9 +175,9 @@ def khop_graph_set_tuning(g, t: khop_tuning) -> None:
     check(lib().khop_graph_set_tuning(g, ctypes.byref(t)), "khop_graph_set_tuning")
 
 
-def khop_autotune(g, seeds, nq, k, stream) -> khop_tuning:
+def khop_autotune(g, seeds, ks, nq, k, stream) -> khop_tuning:
     t = khop_tuning()
-    check(lib().khop_autotune(g, seeds, nq, k, stream, ctypes.byref(t)), "khop_autotune")
+    check(lib().khop_autotune(g, seeds, ks, nq, k, stream, ctypes.byref(t)), "khop_autotune")
     return t
 
 
@@ -395,9 +395,12 @@ class Graph:
                       _stream_ptr(stream))
         return res
 
-    def autotune(self, seeds, k, stream=None) -> khop_tuning:
+    def autotune(self, seeds, k=None, ks=None, stream=None) -> khop_tuning:
+        """Tune on these seeds with one k for all, or per-seed ks."""
         s = self._u32(seeds)
-        return khop_autotune(self.handle, s.data_ptr(), s.numel(), int(k), _stream_ptr(stream))
+        kk = self._u32(ks) if ks is not None else None
+        return khop_autotune(self.handle, s.data_ptr(), kk.data_ptr() if kk is not None else None,
+                             s.numel(), int(k or 0), _stream_ptr(stream))
 
 
 def stats_records(stats_tensor) -> np.ndarray:
