@@ -120,43 +120,63 @@ __global__ void csc_scatter_kernel(const E *rp, const uint32_t *ci, uint64_t n, 
     }
 }
 
-// Sort each CSC column of at most kSortMax in-neighbours ascending (one
-// thread per column, shell sort), so that the order does not depend on the
-// scatter's atomics and neighbouring ids share bitmap words.  Longer columns
-// keep the scatter order; no count depends on the order.
+// In-list order.  A pull round stops at the first in-neighbour in the
+// frontier, and high-degree vertices join the frontier early, so every in-list
+// of at most kSortMax entries is sorted by the in-neighbour's out-degree,
+// highest first (ties by id).  Each entry gets a 64-bit key -- inverted
+// degree above, id below -- in a temporary array; one thread shell-sorts one
+// list's keys; the ids are written back.  Longer lists keep their order.  No
+// count depends on the order; it only shortens pull scans.
 constexpr uint64_t kSortMax = 2048;
-__global__ void csc_sort_kernel32(const uint32_t *cp, uint32_t *ri, uint64_t n) {
+
+template <typename E>
+__global__ void inlist_keys_kernel(const E *rp, const uint32_t *ri, uint64_t m,
+                                   unsigned long long *key) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint32_t *x = ri + cp[v];
-        const uint64_t d = cp[v + 1] - cp[v];
-        if (d > kSortMax) continue;
-        for (uint64_t gap = d / 2; gap > 0; gap = gap == 2 ? 1 : gap * 5 / 11) {
-            for (uint64_t i = gap; i < d; ++i) {
-                const uint32_t t = x[i];
-                uint64_t j = i;
-                while (j >= gap && x[j - gap] > t) { x[j] = x[j - gap]; j -= gap; }
-                x[j] = t;
-            }
-        }
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t u = ri[e];
+        const uint64_t d = (uint64_t)(rp[u + 1] - rp[u]);
+        const uint64_t inv = 0xffffffffull - (d < 0xffffffffull ? d : 0xffffffffull);
+        key[e] = (inv << 32) | u;
     }
 }
 
-__global__ void csc_sort_kernel64(const unsigned long long *cp, uint32_t *ri, uint64_t n) {
+template <typename E>
+__global__ void inlist_sort_kernel(const E *cp, unsigned long long *key, uint32_t *ri, uint64_t n) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint32_t *x = ri + cp[v];
-        const uint64_t d = cp[v + 1] - cp[v];
-        if (d > kSortMax) continue;
+        const uint64_t b = cp[v], d = (uint64_t)cp[v + 1] - b;
+        if (d < 2 || d > kSortMax) continue;
+        unsigned long long *x = key + b;
         for (uint64_t gap = d / 2; gap > 0; gap = gap == 2 ? 1 : gap * 5 / 11) {
             for (uint64_t i = gap; i < d; ++i) {
-                const uint32_t t = x[i];
+                const unsigned long long t = x[i];
                 uint64_t j = i;
                 while (j >= gap && x[j - gap] > t) { x[j] = x[j - gap]; j -= gap; }
                 x[j] = t;
             }
         }
+        for (uint64_t i = 0; i < d; ++i) ri[b + i] = (uint32_t)x[i];
     }
+}
+
+// Sort the in-lists (CSC columns; for a symmetric graph, the CSR rows).
+template <typename E>
+cudaError_t order_inlists(khop_graph *g, const E *cp, uint32_t *ri, cudaStream_t st) {
+    if (g->nnz == 0) return cudaSuccess;
+    unsigned long long *key = nullptr;
+    cudaError_t e = cudaMalloc(&key, g->nnz * sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+    const int blocks = g->num_sms * 8;
+    inlist_keys_kernel<E><<<blocks, 256, 0, st>>>((const E *)g->rp, ri, g->nnz, key);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        inlist_sort_kernel<E><<<blocks, 128, 0, st>>>(cp, key, ri, g->n);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(key);
+    return e != cudaSuccess ? e : e2;
 }
 
 template <typename E>
@@ -182,13 +202,9 @@ cudaError_t build_csc(khop_graph *g, cudaStream_t st) {
         csc_scatter_kernel<E><<<blocks, 256, 0, st>>>((const E *)g->rp, g->ci, n, cursor, ri);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && nnz) {
-        if (sizeof(E) == 4) csc_sort_kernel32<<<blocks, 128, 0, st>>>((const uint32_t *)cp, ri, n);
-        else csc_sort_kernel64<<<blocks, 128, 0, st>>>((const unsigned long long *)cp, ri, n);
-        e = cudaGetLastError();
-    }
     cudaError_t e2 = cudaStreamSynchronize(st);
     cudaFree(cursor);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = order_inlists<E>(g, cp, ri, st);
     return e != cudaSuccess ? e : e2;
 }
 
@@ -502,6 +518,9 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
     if (g->symmetric) {
         g->cp = g->rp;
         g->ri = g->ci;
+        e = g->ewidth == 4 ? order_inlists<uint32_t>(g, (const uint32_t *)g->rp, g->ci, st)
+                           : order_inlists<unsigned long long>(g, (const unsigned long long *)g->rp, g->ci, st);
+        if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
     } else {
         e = g->ewidth == 4 ? build_csc<uint32_t>(g, st) : build_csc<unsigned long long>(g, st);
         if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
