@@ -76,9 +76,9 @@ def paper_queries(g, scale_seeds=1.0):
     return np.concatenate(seeds).astype(np.uint32), np.concatenate(ks)
 
 
-KERNEL_SOURCES = {
-    "plain_kernel": ("khop_plain.cu", "khop_internal.cuh"),
-    "batch_kernel": ("khop_batch.cu", "khop_internal.cuh"),
+KERNEL_SOURCES = {   # a kernel's code and the graph layout it reads
+    "plain_kernel": ("khop_plain.cu", "khop_internal.cuh", "khop_graph.cu"),
+    "batch_kernel": ("khop_batch.cu", "khop_internal.cuh", "khop_graph.cu"),
 }
 
 
