@@ -127,6 +127,7 @@ typedef struct {
     int32_t push_tile;        /* edges per push tile: power of two, 256 .. 8192   */
     float batch_alpha;        /* alpha for the 64-lane batched traversal          */
     float batch_beta;         /* beta for the 64-lane batched traversal           */
+    int32_t batch_push_tile;  /* edges per push tile of the batched traversal: power of two, 256 .. 8192 */
 } khop_tuning;
 
 int khop_graph_get_tuning(const khop_graph *g, khop_tuning *t);
@@ -134,8 +135,8 @@ int khop_graph_set_tuning(khop_graph *g, const khop_tuning *t);
 
 /*
  * Pick tuning values for this graph by timing candidate settings -- grid
- * shape, push tile, alpha and beta of the plain path, then alpha and beta of
- * the batched path -- on `nq` queries (device array `seeds`; per-seed hops in
+ * shape, push tile, alpha and beta of the plain path, then alpha, beta and
+ * push tile of the batched path -- on `nq` queries (device array `seeds`; per-seed hops in
  * the device array `ks`, or, if ks is NULL, `k` for every seed), keeping the
  * fastest of each, and apply them.  Synchronises `stream`.  Never changes a
  * count.

@@ -205,6 +205,13 @@ extern "C" int khop_autotune(khop_graph *g, const uint32_t *seeds, const uint32_
         if (ms < bbest) { bbest = ms; bbe = be; }
     }
     t.batch_beta = bbe;
+    int btile = t.batch_push_tile;
+    for (int tile : {1024, 2048, 4096}) {
+        t.batch_push_tile = tile;
+        const float ms = time_batch(g, seeds, ks, nq, out, st, a, b, &rc);
+        if (ms < bbest) { bbest = ms; btile = tile; }
+    }
+    t.batch_push_tile = btile;
     t.direction = dir0;
     e = cudaStreamSynchronize(st);
     cudaFree(out);

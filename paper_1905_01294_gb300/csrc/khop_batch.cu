@@ -213,6 +213,7 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E> &a, const Round<E
 
 // Visit w for the lanes in m: returns true if w entered the union frontier
 // (its first frontier lane this round) and has out-edges; d = out-degree.
+// The degree is read only for that first entry.
 template <typename E>
 __device__ __forceinline__ bool visit(const BatchArgs<E> &a, const Round<E> &R, uint32_t w,
                                       unsigned long long m, E &d) {
@@ -220,9 +221,9 @@ __device__ __forceinline__ bool visit(const BatchArgs<E> &a, const Round<E> &R, 
     if (!x) return false;
     const unsigned long long nb = x & ~atomicOr(&a.V[w], x);
     if (!nb || R.last) return false;
+    if (atomicOr(&R.Fout[w], nb) != 0ull) return false;
     d = a.rp[w + 1] - a.rp[w];
-    if (d == 0) return false;   // a frontier vertex without out-edges is never read
-    return atomicOr(&R.Fout[w], nb) == 0ull;
+    return d > 0;
 }
 
 // Push round.  Round 1 expands the lanes' seeds straight from the lane table
@@ -794,7 +795,7 @@ BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, con
     a.alpha = g->tune.batch_alpha;
     a.beta = g->tune.batch_beta;
     uint32_t tl = 0;
-    while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
+    while ((1u << tl) < (uint32_t)g->tune.batch_push_tile) ++tl;
     a.tile_log2 = tl;
     a.ebits = g->ebits;
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;

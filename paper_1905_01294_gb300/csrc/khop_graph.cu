@@ -561,6 +561,7 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
     g->tune.push_tile = 2048;
     g->tune.batch_alpha = 14.0f;
     g->tune.batch_beta = 24.0f;
+    g->tune.batch_push_tile = 2048;
     *out = g;
     return KHOP_OK;
 }
@@ -602,6 +603,9 @@ int khop_graph_set_tuning(khop_graph *g, const khop_tuning *t) {
     if (t->push_tile && (t->push_tile < 256 || t->push_tile > 8192 ||
                          (t->push_tile & (t->push_tile - 1))))
         return KHOP_EINVAL;
+    if (t->batch_push_tile && (t->batch_push_tile < 256 || t->batch_push_tile > 8192 ||
+                               (t->batch_push_tile & (t->batch_push_tile - 1))))
+        return KHOP_EINVAL;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tune.direction = t->direction;
     if (t->alpha > 0) g->tune.alpha = t->alpha;
@@ -611,6 +615,7 @@ int khop_graph_set_tuning(khop_graph *g, const khop_tuning *t) {
     if (t->push_tile) g->tune.push_tile = t->push_tile;
     if (t->batch_alpha > 0) g->tune.batch_alpha = t->batch_alpha;
     if (t->batch_beta > 0) g->tune.batch_beta = t->batch_beta;
+    if (t->batch_push_tile) g->tune.batch_push_tile = t->batch_push_tile;
     return KHOP_OK;
 }
 

@@ -54,7 +54,8 @@ class khop_tuning(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_float), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("push_tile", ctypes.c_int32),
-                ("batch_alpha", ctypes.c_float), ("batch_beta", ctypes.c_float)]
+                ("batch_alpha", ctypes.c_float), ("batch_beta", ctypes.c_float),
+                ("batch_push_tile", ctypes.c_int32)]
 
 
 class khop_query_stats(ctypes.Structure):
@@ -337,7 +338,7 @@ class Graph:
         cur = self.tuning()
         t.direction = kw.get("direction", cur.direction)
         for f in ("alpha", "beta", "block_threads", "blocks_per_sm", "push_tile",
-                  "batch_alpha", "batch_beta"):
+                  "batch_alpha", "batch_beta", "batch_push_tile"):
             setattr(t, f, kw.get(f, 0))
         khop_graph_set_tuning(self.handle, t)
 

@@ -76,7 +76,7 @@ def test_direction_extremes(alpha, beta, tile):
     g = gen.rmat(11, 16, seed=6)
     seeds = gen.seeds(g, 200, seed=7)
     ks = gen.mixed_ks(200, choices=(1, 2, 3, 4, 6), seed=8)
-    assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=beta, push_tile=tile) == 0
+    assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=beta, batch_push_tile=tile) == 0
 
 
 def test_edge_cases_k0_bad_seed_duplicates_and_sinks():

@@ -275,6 +275,7 @@ def test_autotune_changes_speed_only():
     t = G.autotune(seeds, 6)
     assert t.block_threads in (256, 512, 1024) and t.push_tile in (512, 1024, 2048, 4096)
     assert t.alpha > 0 and t.beta > 0 and t.batch_alpha > 0 and t.batch_beta > 0
+    assert t.batch_push_tile in (1024, 2048, 4096)
     want, _ = oracle.khop_counts(g, seeds, 6)
     np.testing.assert_array_equal(before, want)
     np.testing.assert_array_equal(kh.as_u64(G.count(seeds, 6)), want)
