@@ -557,6 +557,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     // harvest.  A launch that did not finish leaves `dirty` set, and the next
     // one starts from zeroed buffers.  Both words are read before the
     // prologue barrier and written only after it, so every CTA sees the same.
+    unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
     const bool dirty = ld_volatile_u32(&a.ctl->dirty) != 0u;
     uint64_t rdone = dirty ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
     if (dirty)
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             a.F2[v] = 0ull;
             a.V[v] = 0ull;
         }
-    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
     if (gtid == 0) a.ctl->dirty = 1u;
     const uint64_t nb_total = *a.nbatches;
     uint64_t bytes = 0, nrounds = 0, npull = 0;   // algorithmic HBM bytes, rounds run
@@ -649,20 +650,20 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             else {
                 pull_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
                 // deferred long in-lists (counts read after a barrier: uniform)
-                if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout + 5,
+                if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout + 5,
                                   sh.slot + 5, 2, a.timeout_ns))
                     return;
                 const uint64_t nitems = min((uint64_t)sh.slot[5], a.hcap);
                 if (nitems) {
                     pull_chunks<E>(a, R, min((uint64_t)sh.slot[6], a.ccap), sh);
-                    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0,
+                    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0,
                                       a.timeout_ns))
                         return;
                     pull_settle<E>(a, R, nitems, sh, st_w, st_pre, st_d);
                 }
             }
             flush_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout, sh.slot, 5,
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot, 5,
                               a.timeout_ns))
                 return;
             const uint64_t W = sizeof(E);
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
         bytes += 16ull * a.n;
         unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * 64;
         harvest(a.V, a.n, part + (uint64_t)blockIdx.x * 64, s_lane);
-        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
         if (blockIdx.x == 0) {
             // lane l is summed by the threads l, l + 64, ... over the CTAs
             __shared__ unsigned long long s_sum[kBlock];

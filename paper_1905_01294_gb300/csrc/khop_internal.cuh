@@ -39,6 +39,23 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
+// Asynchronous global -> shared copy of N bytes (4, 8 or 16; both addresses
+// N-aligned), completed by cp_async_wait_all() of the same thread.
+template <int N>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p) {
     return *(const volatile unsigned *)p;
 }
@@ -82,30 +99,48 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // counter.  Every CTA adds to one 32-bit word -- CTA 0 adds 2^31 - (G - 1),
 // the other G - 1 CTAs add 1 -- so the barrier's additions total exactly 2^31:
 // the top bit flips when, and only when, the last CTA has arrived, and the low
-// bits return to where they were (no reset is ever needed).  After a CTA-wide
-// __syncthreads, thread 0 publishes the CTA's writes with a gpu-scope release
-// atomic arrival, then polls the word with acquire loads until the top bit
-// differs from the value its own atomic returned.  The wait is
+// bits return to where they were (no reset is ever needed).  Each CTA's
+// thread 0 keeps the top bit it expects in `sense` (read once at kernel start
+// with barrier_sense(): the bit cannot flip before every CTA, this one
+// included, has arrived).  After a CTA-wide __syncthreads, thread 0 publishes
+// the CTA's writes with a gpu-scope release reduction (no reply to wait for)
+// and polls the word with acquire loads until the top bit flips.  The wait is
 // bounded by `timeout_ns` of %globaltimer and by an iteration cap; on expiry
 // (or if another CTA already flagged a timeout) it sets KHOP_DEVERR_TIMEOUT in
 // *err and returns false, and the caller leaves the kernel.
 // If `post_n` > 0, thread 0 copies post_n 64-bit words from `post_src`
 // (global, written before the barrier) to `post_dst` (shared) after the
 // wait, so the rest of the CTA reads them from shared memory.
+// `overlap(t, nt)` runs on threads 32 .. blockDim.x - 1 (t = threadIdx.x - 32,
+// nt = blockDim.x - 32) while thread 0 waits: work that needs no ordering
+// against the barrier (prefetches).
+__device__ __forceinline__ unsigned barrier_sense(const BarrierWords *bw) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&bw->count) : "memory");
+    return v & 0x80000000u;
+}
+
+struct NoOverlap {
+    __device__ void operator()(unsigned, unsigned) const {}
+};
+
+template <typename Overlap = NoOverlap>
 __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, int *s_flag,
+                                             unsigned &sense,
                                              const unsigned long long *post_src = nullptr,
                                              unsigned long long *post_dst = nullptr,
-                                             int post_n = 0, uint64_t timeout_ns = 2000000000ull) {
+                                             int post_n = 0, uint64_t timeout_ns = 2000000000ull,
+                                             const Overlap &overlap = Overlap()) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        unsigned old;   // the arrival is a release: the CTA's writes precede it
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
-                     : "=r"(old) : "l"(&bw->count), "r"(add) : "memory");
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bw->count), "r"(add)
+                     : "memory");
+        sense ^= 0x80000000u;
         const uint64_t t0 = globaltimer_ns();
         uint64_t spins = 0;
-        while (((ld_acquire_u32(&bw->count) ^ old) & 0x80000000u) == 0u) {
+        while ((ld_acquire_u32(&bw->count) & 0x80000000u) != sense) {
             ++spins;
             if ((spins & 255u) == 0u) {
                 if (ld_volatile_u32(err) & KHOP_DEVERR_TIMEOUT) { ok = 0; break; }
@@ -119,6 +154,8 @@ __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, in
         fence_acq_rel_gpu();
         for (int i = 0; i < post_n; ++i) post_dst[i] = ld_relaxed_u64(post_src + i);
         *s_flag = ok;
+    } else if (threadIdx.x >= 32) {
+        overlap(threadIdx.x - 32u, blockDim.x - 32u);
     }
     __syncthreads();
     return *s_flag != 0;
@@ -144,6 +181,7 @@ struct CtlBlock {
     RoundSlot slot[3];
     unsigned long long pad[4];      // batched path: [0] batches, [1] algorithmic bytes,
                                     // [2] rounds, [3] pull rounds
+    unsigned long long handoff[16]; // plain path: state left by the one-CTA rounds
     BarrierWords bar;
     // Kept across launches (a launch clears only what comes before `err`):
     unsigned err;                   // sticky khop_device_error bits

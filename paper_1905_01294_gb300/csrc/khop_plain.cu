@@ -24,7 +24,12 @@ namespace {
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 
 constexpr int kPushUnroll = 4;   // edges in flight per thread in a push tile
-constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big read V before test-and-set
+constexpr uint64_t kPrefetchEdges = 2048;    // next-query seed edges warmed into L2
+constexpr uint32_t kSoloEdges = 2048;        // 1-hop queries with at most this many seed
+                                             // out-edges run on one CTA
+constexpr uint64_t kSoloRun = 8192;          // queries one CTA answers before the grid regroups
+constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
+                                             // vertices are visited) read V before test-and-set
 constexpr int kPullWords = 4;    // bitmap words a warp works on at once in a pull round
 constexpr int kFlatILP = 4;      // in-edges per lane per step of the flattened pull scan
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
@@ -86,6 +91,8 @@ struct Round {
     unsigned long long *qpack_out;
     uint64_t cap;            // queue items this round may write
     uint64_t items_in, mf;   // input frontier: queue items, out-edges
+    bool solo;               // push round of one tile that fits the staging area: one CTA
+                             // discovers everything, so its queue starts at 0 (no atomic)
 };
 
 // Per-CTA shared state of a round.
@@ -196,9 +203,15 @@ __device__ __forceinline__ void flush_round(const PlainArgs<E> &a, const Round<E
         unsigned long long st = sh.stage;
         if (sh.limit < st) st = sh.limit;   // staged items are the prefix before the first miss
         const uint32_t nst = (uint32_t)(st >> kStagePosShift);
-        if (nst)
-            sh.gbase = atomicAdd(R.qpack_out, ((unsigned long long)nst << a.ebits) +
-                                                  (st & kStageEdgeMask));
+        if (nst) {
+            const unsigned long long add = ((unsigned long long)nst << a.ebits) + (st & kStageEdgeMask);
+            if (R.solo) {
+                sh.gbase = 0ull;
+                *R.qpack_out = add;
+            } else {
+                sh.gbase = atomicAdd(R.qpack_out, add);
+            }
+        }
         if (sh.skipped) atomicAdd(R.qpack_out, sh.skipped << a.ebits);
         sh.skipped = 0;
         sh.qfull = 0;
@@ -227,7 +240,10 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
     const uint32_t tl = a.tile_log2;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
-    for (uint64_t j = blockIdx.x; j < ntiles; j += gridDim.x) {
+    // CTA 0 writes the query results between queries: it takes tile G - 1,
+    // and CTA c > 0 takes tile c - 1 (small rounds have one tile).
+    const uint64_t rank = blockIdx.x == 0 ? gridDim.x - 1u : blockIdx.x - 1u;
+    for (uint64_t j = rank; j < ntiles; j += gridDim.x) {
         const uint64_t e0 = j << tl;
         const uint64_t e1 = min(e0 + T, R.mf);
         uint32_t nitems;
@@ -269,14 +285,25 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
 #pragma unroll
             for (int u = 0; u < kPushUnroll; ++u) {
                 bool disc = false;
+                E rs = 0, re = 0;
+                // Round 1: every distinct neighbour of the seed is new, so its
+                // row offsets are loaded alongside the test-and-set.
+                const bool early = R.first && !R.last && ok[u];
+                if (early) {
+                    rs = a.rp[w[u]];
+                    re = a.rp[w[u] + 1];
+                }
                 if (ok[u]) {
                     const uint32_t wi = w[u] >> 5, bit = 1u << (w[u] & 31);
                     if (!R.precheck || !(R.V[wi] & bit)) disc = !(atomicOr(&R.V[wi], bit) & bit);
                 }
-                E rs = 0, d = 0;
+                E d = 0;
                 if (disc && !R.last) {
-                    rs = a.rp[w[u]];
-                    d = a.rp[w[u] + 1] - rs;
+                    if (!early) {
+                        rs = a.rp[w[u]];
+                        re = a.rp[w[u] + 1];
+                    }
+                    d = re - rs;
                 }
                 record(a, R, disc, w[u], rs, d, true, sh, st_pre, st_rs, st_d);
             }
@@ -310,7 +337,7 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
 #pragma unroll
         for (int j = 0; j < kPullWords; ++j) {
             const uint64_t i = i0 + j;
-            Vw[j] = i < a.nw ? R.V[i] : ~0u;
+            Vw[j] = i < a.nw ? (R.V[i] | a.noin[i]) : ~0u;
             const uint64_t v = (i << 5) + (uint64_t)lane;
             unv[j] = i < a.nw && v < a.n && !((Vw[j] >> lane) & 1u);
             found[j] = false;
@@ -453,15 +480,109 @@ __device__ __forceinline__ uint64_t skip_trivial(const PlainArgs<E> &a, uint64_t
     return q;
 }
 
-// Visited bitmap for the next query: the vertices without in-edges (no round
-// can reach them, so marking them spares the pull sweeps) plus the seed of
-// query q.  Grid-stride over the words.
+// Visited bitmap for the next query: just its seed (stores only).  Pull
+// rounds treat the vertices without in-edges as visited too -- no round can
+// reach them -- by OR-ing in that bitmap as they read V.  Grid-stride over the
+// words.
 template <typename E>
 __device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V, bool any,
                                              uint32_t seed, uint64_t gtid, uint64_t gthreads) {
     const uint64_t sw = any ? (uint64_t)(seed >> 5) : ~0ull;
     const uint32_t sb = 1u << (seed & 31);
-    for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = a.noin[i] | (i == sw ? sb : 0u);
+    for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = i == sw ? sb : 0u;
+}
+
+// A query that one CTA answers alone: k = 1 and at most kSoloEdges out-edges
+// at the seed.  Its single round (q_1 = A^T e_s minus the seed) needs no
+// frontier, no queue and no grid barrier; the other CTAs wait at one barrier
+// for the whole run of such queries.  (Pull-only mode keeps the grid path.)
+template <typename E>
+__device__ __forceinline__ bool solo_query(const QueryHead<E> &h, bool all_pull) {
+    return !all_pull && h.k == 1 && (uint64_t)(h.re - h.rs) <= (uint64_t)kSoloEdges;
+}
+
+// Answer solo queries from query q on, on this CTA only, until the next one
+// is not solo (or kSoloRun were answered or the list ends).  V holds just the
+// seed of query q on entry; each query test-and-sets its seed's out-
+// neighbours, counts the new ones, then stores zero to every word it touched,
+// so V is clean again and gets the next seed's bit.  On return q and cur name
+// the next query, V is prepared for it, and thread 0 has left (q, head) in
+// ctl->handoff for the other CTAs.  Thread 0 writes the results (it is b0).
+template <typename E, int BLOCK>
+__device__ __noinline__ void solo_run(const PlainArgs<E> &a, uint32_t *V, uint64_t &q,
+                                      QueryHead<E> &cur, uint64_t &t_prev, Shared &sh) {
+    constexpr int kPer = (int)(kSoloEdges / BLOCK);
+    const int lane = threadIdx.x & 31;
+    for (uint64_t run = 1;; ++run) {
+        QueryHead<E> nxt{0u, 0u, (E)0, (E)0};
+        uint64_t t_dummy = 0;
+        const uint64_t qn = skip_trivial(a, q + 1, false, t_dummy, &nxt);   // loads in flight
+        const uint32_t deg = (uint32_t)(cur.re - cur.rs);
+        uint32_t w[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
+            w[u] = e < deg ? a.ci[(uint64_t)cur.rs + e] : 0u;
+        }
+        unsigned c = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if ((uint32_t)(u * BLOCK) >= deg) break;   // uniform over the CTA
+            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
+            bool disc = false;
+            if (e < deg) {
+                const uint32_t bit = 1u << (w[u] & 31);
+                disc = !(atomicOr(&V[w[u] >> 5], bit) & bit);
+            }
+            c += (unsigned)__popc(__ballot_sync(FULL, disc));
+        }
+        if (lane == 0 && c) atomicAdd(&sh.cnt, (unsigned long long)c);
+        // warm L2 with the next seed's row while the counts settle
+        if (qn < a.nq && threadIdx.x >= 32) {
+            const uint64_t nd = min((uint64_t)(nxt.re - nxt.rs), (uint64_t)kSoloEdges);
+            const uint64_t step = 128 / sizeof(uint32_t);
+            for (uint64_t e = (uint64_t)(threadIdx.x - 32) * step; e < nd; e += (uint64_t)(BLOCK - 32) * step)
+                prefetch_l2(a.ci + (uint64_t)nxt.rs + e);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint64_t cnt = sh.cnt;
+            sh.cnt = 0;
+            const uint64_t now = globaltimer_ns();
+            a.out[q] = cnt;
+            if (a.out_te) a.out_te[q] = deg;
+            if (a.stats) {
+                khop_query_stats st{t_prev, now, (uint64_t)deg, 4ull * deg + 2ull * sizeof(E), 1u, 0u};
+                a.stats[q] = st;
+            }
+            if (a.per_hop) {
+                for (uint32_t r = 0; r < a.hop_stride; ++r)
+                    a.per_hop[q * a.hop_stride + r] = r == 0 ? 1ull : (r == 1 ? cnt : 0ull);
+            }
+            t_prev = now;
+            if (qn > q + 1)   // answer the trivial queries up to qn
+                skip_trivial(a, q + 1, true, t_prev, (QueryHead<E> *)nullptr);
+        }
+        // clean V: only this query's seed and heads have bits in it
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
+            if (e < deg) V[w[u] >> 5] = 0u;
+        }
+        if (threadIdx.x == 0) V[cur.s >> 5] = 0u;
+        __syncthreads();
+        q = qn;
+        cur = nxt;
+        if (q < a.nq && threadIdx.x == 0) V[cur.s >> 5] = 1u << (cur.s & 31);
+        if (q >= a.nq || !solo_query(cur, false) || run >= kSoloRun) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.ctl->handoff[0] = q;
+        a.ctl->handoff[1] = (unsigned long long)cur.s | ((unsigned long long)cur.k << 32);
+        a.ctl->handoff[2] = (unsigned long long)cur.rs;
+        a.ctl->handoff[3] = (unsigned long long)cur.re;
+    }
 }
 
 template <typename E, int BLOCK>
@@ -485,12 +606,13 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         sh.qfull = 0;
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
+    unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
     __syncthreads();
 
     const bool all_pull = a.direction == KHOP_DIR_PULL;
     unsigned long long *slots = (unsigned long long *)a.ctl->slot;
 
-    // Launch prologue: frontier bitmaps zero, V0 = noin | {first seed}.
+    // Launch prologue: frontier bitmaps zero, V0 = {first seed}.
     QueryHead<E> cur{0u, 0u, (E)0, (E)0}, nxt{0u, 0u, (E)0, (E)0};
     uint64_t q = skip_trivial(a, 0, b0, t_prev, &cur);
     for (uint64_t i = gtid; i < a.nw; i += gthreads) {
@@ -499,11 +621,23 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         a.F2[i] = 0u;
     }
     prep_visited(a, a.V0, q < a.nq, cur.s, gtid, gthreads);
-    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns)) return;
+    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
 
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
     unsigned par = 0;     // which visited bitmap the current query uses
     while (q < a.nq) {
+        if (solo_query(cur, all_pull)) {
+            if (blockIdx.x == 0) solo_run<E, BLOCK>(a, par ? a.V1 : a.V0, q, cur, t_prev, sh);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, a.ctl->handoff, sh.slot, 4,
+                              a.timeout_ns))
+                return;
+            q = sh.slot[0];
+            cur.s = (uint32_t)sh.slot[1];
+            cur.k = (uint32_t)(sh.slot[1] >> 32);
+            cur.rs = (E)sh.slot[2];
+            cur.re = (E)sh.slot[3];
+            continue;
+        }
         const uint32_t s = cur.s;
         const uint32_t k = cur.k;
         uint32_t *V = par ? a.V1 : a.V0;
@@ -514,7 +648,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             uint32_t *Fs = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
             const uint64_t sw = s >> 5;
             for (uint64_t i = gtid; i < a.nw; i += gthreads) Fs[i] = i == sw ? 1u << (s & 31) : 0u;
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, nullptr, nullptr, 0, a.timeout_ns))
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns))
                 return;
         }
         uint64_t mf = (uint64_t)(cur.re - cur.rs);   // out-edges of the frontier {s}
@@ -540,11 +674,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                     dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap)
                               ? DIR_PUSH : DIR_PULL;
             }
-            // Zero what round r+1 writes (last read in round r-1); in round 1
-            // also prepare the next query's visited bitmap.
+            // Zero what round r+1 writes (last read in round r-1).
             uint32_t *Fz = sel3(a.F0, a.F1, a.F2, izero);
             for (uint64_t i = gtid; i < a.nw; i += gthreads) Fz[i] = 0u;
-            if (r == 1) prep_visited(a, Vnext, qn < a.nq, nxt.s, gtid, gthreads);
             if (b0) {
                 slots[kSlotWords * izero + 0] = 0ull;
                 slots[kSlotWords * izero + 1] = 0ull;
@@ -556,7 +688,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             Round<E> R;
             R.first = r == 1;
             R.last = r == k;
-            R.precheck = mf > kPrecheckEdges;
+            R.precheck = mf > kPrecheckEdges && visited * 32 > a.n;
             R.seed = s;
             R.seed_rs = cur.rs;
             R.V = V;
@@ -572,11 +704,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
             R.items_in = items;
             R.mf = mf;
+            R.solo = dir == DIR_PUSH && a.stage &&
+                     mf <= min((uint64_t)1 << a.tile_log2, (uint64_t)kStage);
             if (dir == DIR_PUSH) push_round<E, BLOCK>(a, R, s_pre, s_rs, sh, st_pre, st_rs, st_d);
             else pull_round<E, BLOCK>(a, R, sh, s_winc, s_wpos, st_pre, st_rs, st_d);
+            // Round 1 also prepares the next query's visited bitmap (after the
+            // round's own work, so the look-ahead loads have landed by then).
+            if (r == 1) prep_visited(a, Vnext, qn < a.nq, nxt.s, gtid, gthreads);
             flush_round<E, BLOCK>(a, R, sh, st_pre, st_rs, st_d, slots + kSlotWords * iout);
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, slots + kSlotWords * iout, sh.slot, 4,
-                              a.timeout_ns))
+            // After the last round only CTA 0 (which writes the result) needs
+            // the counters.  While the barrier of round 1 waits, the last CTA
+            // pulls the next query's seed row and its heads' row offsets into
+            // L2 (prefetch only: nothing of that query is computed yet).
+            const bool pf = r == 1 && qn < a.nq && blockIdx.x == gridDim.x - 1;
+            const E pf_rs = nxt.rs;
+            const uint64_t pf_d = min((uint64_t)(nxt.re - nxt.rs), (uint64_t)kPrefetchEdges);
+            const auto prefetch_next = [&](unsigned t, unsigned nt) {
+                if (!pf) return;
+                for (uint64_t e = t; e < pf_d; e += nt) prefetch_l2(a.rp + a.ci[(uint64_t)pf_rs + e]);
+            };
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot,
+                              (R.last && blockIdx.x != 0) ? 0 : 4, a.timeout_ns, prefetch_next))
                 return;
             const unsigned long long qp = sh.slot[0];
             const uint64_t nnew = sh.slot[1];
@@ -588,7 +736,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             } else {
                 const uint64_t seen = visited + a.n_noin;
                 const uint64_t unvisited = a.n > seen ? a.n - seen : 0;
-                bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn +
+                bytes += 3ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn +
                          2ull * W * items_out;
             }
             sum_mf += mf;
@@ -616,7 +764,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                     a.per_hop[q * a.hop_stride + r] = 0ull;
             }
             t_prev = now;
-            skip_trivial(a, q + 1, true, t_prev, (QueryHead<E> *)nullptr);   // answer the trivial queries up to qn
+            if (qn > q + 1)   // answer the trivial queries up to qn
+                skip_trivial(a, q + 1, true, t_prev, (QueryHead<E> *)nullptr);
         }
         q = qn;
         cur = nxt;

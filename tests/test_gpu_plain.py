@@ -165,6 +165,33 @@ def test_hub_rows_many_tiles():
         check_graph(g, seeds, k, push_tile=256)
 
 
+def test_runs_of_small_1hop_queries():
+    """Runs of 1-hop queries at small seeds (answered by one CTA, the rest of
+    the grid waiting) longer than one run, seed degrees on both sides of
+    the one-CTA bound (2048 out-edges) with duplicate heads and self-loops,
+    and other queries (k = 0, k > 1, seeds without out-edges) cutting the
+    runs."""
+    rng = np.random.default_rng(77)
+    n = 5000
+    src, dst = [], []
+    for v, d in ((0, 2048), (1, 2049), (2, 2047), (3, 4000), (4, 1)):
+        heads = rng.integers(0, n, d)
+        heads[: d // 3] = heads[0]          # duplicate heads
+        heads[-1] = v                       # self-loop
+        src.append(np.full(d, v))
+        dst.append(heads)
+    src.append(rng.integers(5, n - 100, 20000))   # the last 100 vertices have no out-edges
+    dst.append(rng.integers(0, n, 20000))
+    g = gen.csr_raw(n, np.concatenate(src), np.concatenate(dst))
+    seeds = rng.integers(0, n, 9000).astype(np.uint32)
+    seeds[:6] = [0, 1, 2, 3, 4, n - 1]
+    ks = np.ones(9000, np.uint32)
+    cut = rng.choice(np.arange(8400, 9000), 60, replace=False)
+    ks[cut] = rng.choice([0, 2, 3, 6], 60)
+    seeds[rng.choice(np.arange(8400, 9000), 10, replace=False)] = n - 3   # no out-edges
+    check_graph(g, seeds, ks, hop=True)
+
+
 def test_edge_cases_seed_out_of_range_and_k0():
     g = gen.rmat(8, 8, seed=1)
     G = kh.Graph.from_csr(g)
