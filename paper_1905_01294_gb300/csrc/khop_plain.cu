@@ -492,59 +492,167 @@ __device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V,
     for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = i == sw ? sb : 0u;
 }
 
+// Look-ahead over the query list for the one-CTA path: the heads of the next
+// queries, fetched by thread 0 with asynchronous copies into a shared-memory
+// ring, so no thread waits on the dependent loads seeds[i] -> rp[seed].  Each
+// query start commits two copy groups -- the row bounds of q + 4 and the seed
+// and k of q + 6 -- and waits only for the groups of two query starts ago, so
+// every copy has two queries' time to land.  After ring_advance(q) the heads
+// of q + 1 and q + 2 are complete and the row of q + 2 is being prefetched
+// into L2 (at most kSoloEdges out-edges of it).
+template <typename E>
+struct Peek {
+    uint32_t s, k;
+    E rs, re;
+};
+constexpr int kRing = 8;
+
+template <typename E>
+__device__ __forceinline__ void ring_stage1(const PlainArgs<E> &a, Peek<E> *ring, uint64_t i) {
+    Peek<E> &p = ring[i % kRing];
+    if (i < a.nq) {
+        cp_async<4>(&p.s, a.seeds + i);
+        if (a.ks) cp_async<4>(&p.k, a.ks + i);
+        else p.k = a.k_all;
+    } else {
+        p.s = 0xffffffffu;
+        p.k = 0u;
+    }
+    cp_async_commit();
+}
+
+template <typename E>
+__device__ __forceinline__ void ring_stage2(const PlainArgs<E> &a, Peek<E> *ring, uint64_t i) {
+    Peek<E> &p = ring[i % kRing];
+    const uint32_t s = p.s;
+    if (i < a.nq && s < a.n) {
+        cp_async<(int)sizeof(E)>(&p.rs, a.rp + s);
+        cp_async<(int)sizeof(E)>(&p.re, a.rp + s + 1);
+    } else {
+        p.rs = (E)0;
+        p.re = (E)0;
+    }
+    cp_async_commit();
+}
+
+template <typename E>
+__device__ __forceinline__ void ring_prefetch_row(const PlainArgs<E> &a, const Peek<E> *ring, uint64_t i) {
+    const Peek<E> &p = ring[i % kRing];
+    if (i < a.nq && p.s < a.n && p.re > p.rs) {
+        const uint64_t nd = min((uint64_t)(p.re - p.rs), (uint64_t)kSoloEdges);
+        for (uint64_t e = 0; e < nd; e += 128 / sizeof(uint32_t)) prefetch_l2(a.ci + (uint64_t)p.rs + e);
+    }
+}
+
+// Thread 0, when query q starts.
+template <typename E>
+__device__ __forceinline__ void ring_advance(const PlainArgs<E> &a, Peek<E> *ring, uint64_t q) {
+    cp_async_wait_group<2>();   // the groups of ring_advance(q - 2) and before
+    ring_stage2(a, ring, q + 4);
+    ring_stage1(a, ring, q + 6);
+    ring_prefetch_row(a, ring, q + 2);
+}
+
+// Thread 0: (re)start the ring in the state ring_advance(q) expects: heads of
+// q + 1 .. q + 3 complete, seeds of q + 4, q + 5 in place (nothing pending).
+template <typename E>
+__device__ __forceinline__ void ring_restart(const PlainArgs<E> &a, Peek<E> *ring, uint64_t q) {
+    cp_async_wait_all();
+    for (uint64_t i = q + 1; i <= q + 5; ++i) ring_stage1(a, ring, i);
+    cp_async_wait_all();
+    for (uint64_t i = q + 1; i <= q + 3; ++i) ring_stage2(a, ring, i);
+    cp_async_wait_all();
+    ring_prefetch_row(a, ring, q + 1);
+}
+
+// The first query after q that needs a traversal (no writes), from the ring's
+// head of q + 1 (complete and published since query q started); scans on
+// only when q + 1 needs no traversal.
+template <typename E>
+__device__ __forceinline__ uint64_t ring_next(const PlainArgs<E> &a, const Peek<E> *ring, uint64_t q,
+                                              QueryHead<E> &h) {
+    if (q + 1 >= a.nq) return a.nq;
+    const Peek<E> &p = ring[(q + 1) % kRing];
+    if (p.s < a.n && p.k > 0 && p.re > p.rs) {
+        h = QueryHead<E>{p.s, p.k, p.rs, p.re};
+        return q + 1;
+    }
+    uint64_t t_dummy = 0;
+    return skip_trivial(a, q + 1, false, t_dummy, &h);
+}
+
 // A query that one CTA answers alone: k = 1 and at most kSoloEdges out-edges
-// at the seed.  Its single round (q_1 = A^T e_s minus the seed) needs no
-// frontier, no queue and no grid barrier; the other CTAs wait at one barrier
-// for the whole run of such queries.  (Pull-only mode keeps the grid path.)
+// at the seed.  Its single round is q_1 = A^T e_s minus the seed, so its
+// count is the number of distinct out-neighbours of s other than s: one CTA
+// finds them with a hash set in shared memory -- no visited bitmap, no
+// frontier, no grid barrier -- while the other CTAs wait at one barrier for
+// the whole run of such queries.  (Pull-only mode keeps the grid path.)
 template <typename E>
 __device__ __forceinline__ bool solo_query(const QueryHead<E> &h, bool all_pull) {
     return !all_pull && h.k == 1 && (uint64_t)(h.re - h.rs) <= (uint64_t)kSoloEdges;
 }
 
-// Answer solo queries from query q on, on this CTA only, until the next one
-// is not solo (or kSoloRun were answered or the list ends).  V holds just the
-// seed of query q on entry; each query test-and-sets its seed's out-
-// neighbours, counts the new ones, then stores zero to every word it touched,
-// so V is clean again and gets the next seed's bit.  On return q and cur name
-// the next query, V is prepared for it, and thread 0 has left (q, head) in
-// ctl->handoff for the other CTAs.  Thread 0 writes the results (it is b0).
+constexpr uint32_t kHashSlots = 2 * kSoloEdges;   // open addressing, load <= 1/2
+constexpr uint32_t kHashEmpty = 0xffffffffu;      // never a vertex id (n < 2^32)
+static_assert(kHashSlots * 4 <= 3 * kStage * 4, "the hash set lives in the staging area");
+
+// Insert w; true if it was not in the set.  Linear probing with CAS.
+__device__ __forceinline__ bool hash_insert(uint32_t *tab, uint32_t w, uint32_t &slot) {
+    uint32_t h = (w * 0x9E3779B1u) >> (32 - 12);   // 12 bits: kHashSlots = 4096
+    for (;;) {
+        const uint32_t old = atomicCAS(&tab[h], kHashEmpty, w);
+        if (old == kHashEmpty) {
+            slot = h;
+            return true;
+        }
+        if (old == w) return false;
+        h = (h + 1) & (kHashSlots - 1);
+    }
+}
+
+// Answer 1-hop queries from query q on, on this CTA only, until the next one
+// is not such a query (or kSoloRun were answered or the list ends).  The
+// visited bitmap V is not used: on entry it holds the seed of query q, on
+// return the seed of the query the grid goes on with.  On return q and cur
+// name that query and thread 0 has left (q, head) in ctl->handoff for the
+// other CTAs.  Thread 0 writes the results (it is b0) and keeps the
+// look-ahead ring.
 template <typename E, int BLOCK>
-__device__ __noinline__ void solo_run(const PlainArgs<E> &a, uint32_t *V, uint64_t &q,
-                                      QueryHead<E> &cur, uint64_t &t_prev, Shared &sh) {
+__device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uint64_t &q,
+                                      QueryHead<E> &cur, uint64_t &t_prev, Shared &sh,
+                                      Peek<E> *ring, uint32_t *tab) {
+    static_assert(kHashSlots == 4096, "hash_insert takes 12 bits");
+    // A private copy: its fields stay in registers (the launch arguments seen
+    // through a reference would be reloaded after every store and copy).
+    const PlainArgs<E> a = args;
     constexpr int kPer = (int)(kSoloEdges / BLOCK);
     const int lane = threadIdx.x & 31;
+    const uint32_t s_first = cur.s;
+    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) tab[i] = kHashEmpty;
+    if (threadIdx.x == 0) ring_restart(a, ring, q);
+    __syncthreads();
     for (uint64_t run = 1;; ++run) {
-        QueryHead<E> nxt{0u, 0u, (E)0, (E)0};
-        uint64_t t_dummy = 0;
-        const uint64_t qn = skip_trivial(a, q + 1, false, t_dummy, &nxt);   // loads in flight
+        if (threadIdx.x == 0) ring_advance(a, ring, q);
         const uint32_t deg = (uint32_t)(cur.re - cur.rs);
         uint32_t w[kPer];
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
-            w[u] = e < deg ? a.ci[(uint64_t)cur.rs + e] : 0u;
+            w[u] = e < deg ? a.ci[(uint64_t)cur.rs + e] : kHashEmpty;
         }
+        uint32_t slot[kPer];
         unsigned c = 0;
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
+            slot[u] = kHashSlots;
             if ((uint32_t)(u * BLOCK) >= deg) break;   // uniform over the CTA
-            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
-            bool disc = false;
-            if (e < deg) {
-                const uint32_t bit = 1u << (w[u] & 31);
-                disc = !(atomicOr(&V[w[u] >> 5], bit) & bit);
-            }
+            const bool disc = w[u] != kHashEmpty && w[u] != cur.s && hash_insert(tab, w[u], slot[u]);
             c += (unsigned)__popc(__ballot_sync(FULL, disc));
         }
         if (lane == 0 && c) atomicAdd(&sh.cnt, (unsigned long long)c);
-        // warm L2 with the next seed's row while the counts settle
-        if (qn < a.nq && threadIdx.x >= 32) {
-            const uint64_t nd = min((uint64_t)(nxt.re - nxt.rs), (uint64_t)kSoloEdges);
-            const uint64_t step = 128 / sizeof(uint32_t);
-            for (uint64_t e = (uint64_t)(threadIdx.x - 32) * step; e < nd; e += (uint64_t)(BLOCK - 32) * step)
-                prefetch_l2(a.ci + (uint64_t)nxt.rs + e);
-        }
-        __syncthreads();
+        __syncthreads();   // counts complete; the ring's heads of q + 1, q + 2 published
+        QueryHead<E> nxt{0u, 0u, (E)0, (E)0};
+        const uint64_t qn = ring_next(a, ring, q, nxt);
         if (threadIdx.x == 0) {
             const uint64_t cnt = sh.cnt;
             sh.cnt = 0;
@@ -560,24 +668,25 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &a, uint32_t *V, uint64
                     a.per_hop[q * a.hop_stride + r] = r == 0 ? 1ull : (r == 1 ? cnt : 0ull);
             }
             t_prev = now;
-            if (qn > q + 1)   // answer the trivial queries up to qn
+            if (qn > q + 1) {   // answer the trivial queries up to qn; restart the look-ahead
                 skip_trivial(a, q + 1, true, t_prev, (QueryHead<E> *)nullptr);
+                if (qn < a.nq) ring_restart(a, ring, qn);
+            }
         }
-        // clean V: only this query's seed and heads have bits in it
+        // empty the slots this query filled
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
-            if (e < deg) V[w[u] >> 5] = 0u;
-        }
-        if (threadIdx.x == 0) V[cur.s >> 5] = 0u;
-        __syncthreads();
+        for (int u = 0; u < kPer; ++u)
+            if (slot[u] < kHashSlots) tab[slot[u]] = kHashEmpty;
         q = qn;
         cur = nxt;
-        if (q < a.nq && threadIdx.x == 0) V[cur.s >> 5] = 1u << (cur.s & 31);
         if (q >= a.nq || !solo_query(cur, false) || run >= kSoloRun) break;
-        __syncthreads();
+        __syncthreads();   // the set is empty again before the next query's inserts
     }
     if (threadIdx.x == 0) {
+        cp_async_wait_all();
+        // V for the grid's next query: its seed only
+        V[s_first >> 5] = 0u;
+        if (q < a.nq) V[cur.s >> 5] = 1u << (cur.s & 31);
         a.ctl->handoff[0] = q;
         a.ctl->handoff[1] = (unsigned long long)cur.s | ((unsigned long long)cur.k << 32);
         a.ctl->handoff[2] = (unsigned long long)cur.rs;
@@ -595,6 +704,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     E *st_d = st_rs + kStage;
     __shared__ Shared sh;
     __shared__ E s_winc[BLOCK], s_wpos[BLOCK];        // flattened pull scan, 32 per warp
+    __shared__ Peek<E> s_ring[kRing];                 // one-CTA look-ahead over the query list
 
     const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
     const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -627,7 +737,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     unsigned par = 0;     // which visited bitmap the current query uses
     while (q < a.nq) {
         if (solo_query(cur, all_pull)) {
-            if (blockIdx.x == 0) solo_run<E, BLOCK>(a, par ? a.V1 : a.V0, q, cur, t_prev, sh);
+            if (blockIdx.x == 0)
+                solo_run<E, BLOCK>(a, par ? a.V1 : a.V0, q, cur, t_prev, sh, s_ring, (uint32_t *)st_pre);
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, a.ctl->handoff, sh.slot, 4,
                               a.timeout_ns))
                 return;
