@@ -28,6 +28,8 @@ constexpr uint64_t kPrefetchEdges = 2048;    // next-query seed edges warmed int
 constexpr uint32_t kSoloEdges = 2048;        // 1-hop queries with at most this many seed
                                              // out-edges run on one CTA
 constexpr uint64_t kSoloRun = 8192;          // queries one CTA answers before the grid regroups
+constexpr uint32_t kFuseDeg = 2048;          // seeds with at most this many out-edges get their
+                                             // first two rounds fused into one grid round
 constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
                                              // vertices are visited) read V before test-and-set
 constexpr int kPullWords = 4;    // bitmap words a warp works on at once in a pull round
@@ -93,6 +95,10 @@ struct Round {
     uint64_t items_in, mf;   // input frontier: queue items, out-edges
     bool solo;               // push round of one tile that fits the staging area: one CTA
                              // discovers everything, so its queue starts at 0 (no atomic)
+    bool fused;              // rounds 1 and 2 in one: the items (the seed's distinct
+                             // out-neighbours) are in shared memory, and heads in that
+                             // set (or the seed) are skipped
+    const uint32_t *nbr;     // fused: hash set of the seed's distinct out-neighbours
 };
 
 // Per-CTA shared state of a round.
@@ -106,8 +112,56 @@ struct Shared {
     unsigned long long skipped;  // items not queued because the queue was past its cap
     int qfull;                   // this CTA saw the queue past its cap (pull rounds)
     unsigned long long slot[4];  // counters of the round just finished
+    unsigned m1;                 // fused round: distinct out-neighbours of the seed
     int flag;
 };
+
+constexpr uint32_t kHashSlots = 4096;             // open addressing over <= 2048 keys
+constexpr uint32_t kHashEmpty = 0xffffffffu;      // never a vertex id (n < 2^32)
+static_assert(kHashSlots * 4 <= 3 * kStage * 4, "the one-CTA hash set lives in the staging area");
+
+__device__ __forceinline__ uint32_t hash_home(uint32_t w) {
+    return (w * 0x9E3779B1u) >> (32 - 12);   // 12 bits: kHashSlots = 4096
+}
+
+// Insert w; true if it was not in the set (slot = where it went).  Linear
+// probing with CAS.
+__device__ __forceinline__ bool hash_insert(uint32_t *tab, uint32_t w, uint32_t &slot) {
+    uint32_t h = hash_home(w);
+    for (;;) {
+        const uint32_t old = atomicCAS(&tab[h], kHashEmpty, w);
+        if (old == kHashEmpty) {
+            slot = h;
+            return true;
+        }
+        if (old == w) return false;
+        h = (h + 1) & (kHashSlots - 1);
+    }
+}
+
+// Insert w if absent; slot = where w is (inserted here or before).
+__device__ __forceinline__ void hash_insert_at(uint32_t *tab, uint32_t w, uint32_t &slot) {
+    uint32_t h = hash_home(w);
+    for (;;) {
+        const uint32_t old = atomicCAS(&tab[h], kHashEmpty, w);
+        if (old == kHashEmpty || old == w) {
+            slot = h;
+            return;
+        }
+        h = (h + 1) & (kHashSlots - 1);
+    }
+}
+
+// Is w in the set (no concurrent inserts)?
+__device__ __forceinline__ bool hash_contains(const uint32_t *tab, uint32_t w) {
+    uint32_t h = hash_home(w);
+    for (;;) {
+        const uint32_t x = tab[h];
+        if (x == w) return true;
+        if (x == kHashEmpty) return false;
+        h = (h + 1) & (kHashSlots - 1);
+    }
+}
 
 // Write queue item `pos` (out-edge prefix pre, row start rs, out-degree d)
 // and point every push tile that begins inside its row at it.
@@ -247,7 +301,17 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
         const uint64_t e0 = j << tl;
         const uint64_t e1 = min(e0 + T, R.mf);
         uint32_t nitems;
-        if (R.first) {
+        uint32_t hint = 0;
+        if (R.fused) {
+            // all items are in shared memory already: start at the tile's first
+            nitems = (uint32_t)R.items_in;
+            uint32_t lo = 0, hi = nitems - 1;   // largest item with prefix <= e0
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if ((uint64_t)s_pre[mid] <= e0) lo = mid; else hi = mid - 1;
+            }
+            hint = lo;
+        } else if (R.first) {
             if (threadIdx.x == 0) {
                 s_pre[0] = (E)0;
                 s_rs[0] = R.seed_rs;
@@ -262,8 +326,7 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
                 s_rs[t] = R.Qrs_in[i0 + t];
             }
         }
-        __syncthreads();
-        uint32_t hint = 0;
+        if (!R.fused) __syncthreads();
         for (uint64_t base = e0; base < e1; base += (uint64_t)BLOCK * kPushUnroll) {
             uint32_t w[kPushUnroll];
             bool ok[kPushUnroll];
@@ -293,7 +356,9 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
                     rs = a.rp[w[u]];
                     re = a.rp[w[u] + 1];
                 }
-                if (ok[u]) {
+                // fused round: the seed and its out-neighbours belong to round 0/1
+                const bool go = ok[u] && !(R.fused && (w[u] == R.seed || hash_contains(R.nbr, w[u])));
+                if (go) {
                     const uint32_t wi = w[u] >> 5, bit = 1u << (w[u] & 31);
                     if (!R.precheck || !(R.V[wi] & bit)) disc = !(atomicOr(&R.V[wi], bit) & bit);
                 }
@@ -308,8 +373,96 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
                 record(a, R, disc, w[u], rs, d, true, sh, st_pre, st_rs, st_d);
             }
         }
-        __syncthreads();
+        if (!R.fused) __syncthreads();
     }
+}
+
+// Prelude of a fused first round, run by every CTA on its own: the seed's
+// distinct out-neighbours other than the seed (q_1 of the paper's iteration,
+// Sec. III) into the shared hash set `tab`, in the order of their first
+// position in the seed's row (the same order in every CTA, so all CTAs cut
+// round 2's edge list the same way), their row starts into s_rs and their
+// out-edge prefix sums into s_pre (s_pre[m1] = m_f of round 2).  `pos` holds
+// each key's first position.  Returns m1 (both tables are emptied by the
+// caller after the round).
+template <typename E, int BLOCK>
+__device__ __forceinline__ uint32_t fused_prelude(const PlainArgs<E> &a, uint32_t s, E rs0,
+                                                  uint32_t deg, uint32_t *tab, uint32_t *pos, E *s_pre,
+                                                  E *s_rs, Shared &sh) {
+    constexpr int kPer = (int)(kFuseDeg / BLOCK);
+    uint32_t *ids = (uint32_t *)s_pre;   // the neighbours' ids, before the prefix sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ E s_wtot[32];
+    // thread t holds row positions t * kPer .. t * kPer + kPer - 1
+    uint32_t w[kPer], slot[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const uint32_t e = threadIdx.x * kPer + u;
+        w[u] = e < deg ? a.ci[(uint64_t)rs0 + e] : kHashEmpty;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        slot[u] = kHashSlots;
+        if (w[u] != kHashEmpty && w[u] != s) {
+            hash_insert_at(tab, w[u], slot[u]);
+            atomicMin(&pos[slot[u]], threadIdx.x * kPer + u);
+        }
+    }
+    __syncthreads();
+    // keep each neighbour at its first position; compact in row order
+    unsigned keep = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+        if (slot[u] < kHashSlots && pos[slot[u]] == threadIdx.x * kPer + u) keep |= 1u << u;
+    const E kc = (E)__popc(keep);
+    E incl = warp_inclusive_sum(kc);
+    if (lane == 31) s_wtot[warp] = incl;
+    __syncthreads();
+    E base = incl - kc, tot = 0;
+    for (int i = 0; i < BLOCK / 32; ++i) {
+        if (i < warp) base += s_wtot[i];
+        tot += s_wtot[i];
+    }
+    const uint32_t m1 = (uint32_t)tot;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+        if ((keep >> u) & 1u) ids[base++] = w[u];
+    __syncthreads();   // ids complete; s_wtot free again
+    // row bounds of the items this thread owns: [t * c, t * c + c)
+    const uint32_t c = (m1 + BLOCK - 1) / BLOCK;
+    const uint32_t i0 = min(threadIdx.x * c, m1), i1 = min(i0 + c, m1);
+    E rsv[kPer], dv[kPer];
+    E local = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        rsv[j] = 0;
+        dv[j] = 0;
+        if (i0 + j < i1) {
+            const uint32_t v = ids[i0 + j];
+            rsv[j] = a.rp[v];
+            dv[j] = a.rp[v + 1] - rsv[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) local += dv[j];
+    // exclusive scan of the per-thread sums over the CTA
+    incl = warp_inclusive_sum(local);
+    if (lane == 31) s_wtot[warp] = incl;
+    __syncthreads();   // also: every thread has read its ids before s_pre is overwritten
+    E wbase = 0;
+    for (int i = 0; i < warp; ++i) wbase += s_wtot[i];
+    E pre = wbase + incl - local;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (i0 + j < i1) {
+            s_pre[i0 + j] = pre;
+            s_rs[i0 + j] = rsv[j];
+            pre += dv[j];
+        }
+    }
+    if (threadIdx.x == BLOCK - 1) s_pre[m1] = pre;   // the last thread's end = the total
+    __syncthreads();
+    return m1;
 }
 
 // Pull round (masked SpMV over the unvisited vertices).  A warp takes
@@ -592,23 +745,7 @@ __device__ __forceinline__ bool solo_query(const QueryHead<E> &h, bool all_pull)
     return !all_pull && h.k == 1 && (uint64_t)(h.re - h.rs) <= (uint64_t)kSoloEdges;
 }
 
-constexpr uint32_t kHashSlots = 2 * kSoloEdges;   // open addressing, load <= 1/2
-constexpr uint32_t kHashEmpty = 0xffffffffu;      // never a vertex id (n < 2^32)
-static_assert(kHashSlots * 4 <= 3 * kStage * 4, "the hash set lives in the staging area");
-
-// Insert w; true if it was not in the set.  Linear probing with CAS.
-__device__ __forceinline__ bool hash_insert(uint32_t *tab, uint32_t w, uint32_t &slot) {
-    uint32_t h = (w * 0x9E3779B1u) >> (32 - 12);   // 12 bits: kHashSlots = 4096
-    for (;;) {
-        const uint32_t old = atomicCAS(&tab[h], kHashEmpty, w);
-        if (old == kHashEmpty) {
-            slot = h;
-            return true;
-        }
-        if (old == w) return false;
-        h = (h + 1) & (kHashSlots - 1);
-    }
-}
+static_assert(kHashSlots == 2 * kSoloEdges, "load factor <= 1/2");
 
 // Answer 1-hop queries from query q on, on this CTA only, until the next one
 // is not such a query (or kSoloRun were answered or the list ends).  The
@@ -621,7 +758,6 @@ template <typename E, int BLOCK>
 __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uint64_t &q,
                                       QueryHead<E> &cur, uint64_t &t_prev, Shared &sh,
                                       Peek<E> *ring, uint32_t *tab) {
-    static_assert(kHashSlots == 4096, "hash_insert takes 12 bits");
     // A private copy: its fields stay in registers (the launch arguments seen
     // through a reference would be reloaded after every store and copy).
     const PlainArgs<E> a = args;
@@ -697,11 +833,14 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
 template <typename E, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainArgs<E> a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    E *s_pre = (E *)dyn_smem;                         // push tile items [T + 2]
-    E *s_rs = s_pre + ((1u << a.tile_log2) + 2u);
-    E *st_pre = s_rs + ((1u << a.tile_log2) + 2u);    // staged queue items [kStage]
+    const uint32_t tcap = max(1u << a.tile_log2, kFuseDeg) + 2u;
+    E *s_pre = (E *)dyn_smem;                         // push tile items [max(T, fused) + 2]
+    E *s_rs = s_pre + tcap;
+    E *st_pre = s_rs + tcap;                          // staged queue items [kStage]
     E *st_rs = st_pre + kStage;
     E *st_d = st_rs + kStage;
+    uint32_t *s_nbr = (uint32_t *)(st_d + kStage);    // fused rounds: hash set [kHashSlots]
+    uint32_t *s_npos = s_nbr + kHashSlots;            //   and each key's first row position
     __shared__ Shared sh;
     __shared__ E s_winc[BLOCK], s_wpos[BLOCK];        // flattened pull scan, 32 per warp
     __shared__ Peek<E> s_ring[kRing];                 // one-CTA look-ahead over the query list
@@ -717,6 +856,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
     unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
+    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+        s_nbr[i] = kHashEmpty;
+        s_npos[i] = 0xffffffffu;
+    }
     __syncthreads();
 
     const bool all_pull = a.direction == KHOP_DIR_PULL;
@@ -796,10 +939,36 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                 slots[kSlotWords * izero + 4] = 0ull;
             }
             te += mf;
+            // Rounds 1 and 2 in one grid round (k >= 2, a push from a small seed
+            // row): every CTA lists q_1 itself, so round 1 needs no barrier.
+            // Not when Beamer's test would pull in round 2.
+            uint32_t m1 = 0;
+            uint64_t mf2 = 0;
+            bool fused = false;
+            if (r == 1 && k >= 2 && !all_pull && a.stage && mf <= (uint64_t)kFuseDeg) {
+                m1 = fused_prelude<E, BLOCK>(a, s, cur.rs, (uint32_t)mf, s_nbr, s_npos, s_pre, s_rs, sh);
+                mf2 = (uint64_t)s_pre[m1];
+                const uint64_t mu = a.nnz - (mf + mf2);
+                fused = a.direction == KHOP_DIR_PUSH || !((double)mf2 * (double)a.alpha > (double)mu);
+                if (fused && blockIdx.x == 0)   // q_1 visited (round 2 skips it)
+                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+                        const uint32_t x = s_nbr[i];
+                        if (x != kHashEmpty) atomicOr(&V[x >> 5], 1u << (x & 31));
+                    }
+                if (!fused) {
+                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+                        s_nbr[i] = kHashEmpty;
+                        s_npos[i] = 0xffffffffu;
+                    }
+                    __syncthreads();
+                }
+            }
             Round<E> R;
-            R.first = r == 1;
-            R.last = r == k;
+            R.first = r == 1 && !fused;
+            R.last = r + (fused ? 1u : 0u) == k;
             R.precheck = mf > kPrecheckEdges && visited * 32 > a.n;
+            R.fused = fused;
+            R.nbr = s_nbr;
             R.seed = s;
             R.seed_rs = cur.rs;
             R.V = V;
@@ -813,10 +982,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.TF_out = qout ? a.TF1 : a.TF0;
             R.qpack_out = slots + kSlotWords * iout;
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
-            R.items_in = items;
-            R.mf = mf;
+            R.items_in = fused ? (uint64_t)m1 : items;
+            R.mf = fused ? mf2 : mf;
             R.solo = dir == DIR_PUSH && a.stage &&
-                     mf <= min((uint64_t)1 << a.tile_log2, (uint64_t)kStage);
+                     R.mf <= min((uint64_t)1 << a.tile_log2, (uint64_t)kStage);
             if (dir == DIR_PUSH) push_round<E, BLOCK>(a, R, s_pre, s_rs, sh, st_pre, st_rs, st_d);
             else pull_round<E, BLOCK>(a, R, sh, s_winc, s_wpos, st_pre, st_rs, st_d);
             // Round 1 also prepares the next query's visited bitmap (after the
@@ -842,6 +1011,30 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             const uint64_t scn = sh.slot[2];
             const uint64_t W = sizeof(E);
             const uint64_t items_out = R.last ? 0 : min((uint64_t)(qp >> a.ebits), R.cap);
+            if (fused) {
+                // rounds 1 and 2: q_1 (m1 vertices) was listed by every CTA
+                for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+                    s_nbr[i] = kHashEmpty;
+                    s_npos[i] = 0xffffffffu;
+                }
+                bytes += 4ull * mf + 2ull * W * (1ull + m1);
+                bytes += 4ull * mf2 + 2ull * W * (m1 + items_out);
+                te += mf2;
+                sum_mf += mf + mf2;
+                count += m1 + nnew;
+                visited += m1 + nnew;
+                nf = nnew;
+                items = qp >> a.ebits;
+                mf = R.last ? 0 : sh.slot[3];
+                prev = DIR_PUSH;
+                rounds = 2;
+                if (b0 && a.per_hop) {
+                    if (a.hop_stride > 1) a.per_hop[q * a.hop_stride + 1] = m1;
+                    if (a.hop_stride > 2) a.per_hop[q * a.hop_stride + 2] = nnew;
+                }
+                r = 2;
+                continue;
+            }
             if (dir == DIR_PUSH) {
                 bytes += 4ull * mf + 2ull * W * ((r == 1 ? 1ull : items) + items_out);
             } else {
@@ -882,6 +1075,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         cur = nxt;
         par ^= 1u;
     }
+}
+
+// Dynamic shared memory of plain_kernel: push tile items, staging area and
+// the fused round's hash set with its first-position table.
+template <typename E>
+size_t plain_smem_bytes(uint32_t tile_log2) {
+    const size_t tcap = std::max<size_t>(size_t(1) << tile_log2, kFuseDeg) + 2;
+    return (2 * tcap + 3 * (size_t)kStage) * sizeof(E) + 2 * (size_t)kHashSlots * sizeof(uint32_t);
 }
 
 template <typename E, int BLOCK>
@@ -949,7 +1150,7 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
                      ? 0ull
                      : std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.beta) + 32);
     a.timeout_ns = g->timeout_ns;
-    const size_t smem = (2 * ((size_t(1) << tl) + 2) + 3 * (size_t)kStage) * sizeof(E);
+    const size_t smem = plain_smem_bytes<E>(tl);
     switch (g->tune.block_threads) {
         case 256: return launch_block<E, 256>(g, a, smem, grid_ctas, st);
         case 1024: return launch_block<E, 1024>(g, a, smem, grid_ctas, st);
@@ -1118,7 +1319,7 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     constexpr int kBlk = 512;
-    const size_t smem = (2 * ((size_t(1) << a.tile_log2) + 2) + 3 * (size_t)kStage) * sizeof(uint32_t);
+    const size_t smem = plain_smem_bytes<uint32_t>(a.tile_log2);
     const void *fn = (const void *)plain_kernel<uint32_t, kBlk>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);

@@ -192,6 +192,33 @@ def test_runs_of_small_1hop_queries():
     check_graph(g, seeds, ks, hop=True)
 
 
+def test_fused_first_rounds_at_the_seed_degree_bound():
+    """Multi-hop queries whose first two rounds run as one grid round (seed
+    out-degree up to 2048: every CTA lists the seed's distinct out-neighbours
+    itself) and the ones just above the bound, with duplicate heads,
+    self-loops, sinks among the neighbours, and heads that are also
+    neighbours of neighbours; counts, TE and per-hop counts in all three
+    direction modes."""
+    rng = np.random.default_rng(91)
+    n = 6000
+    src, dst = [], []
+    for v, d in ((0, 2048), (1, 2049), (2, 2047), (3, 5), (4, 1)):
+        heads = rng.integers(0, 600, d)     # a dense neighbourhood: many shared heads
+        heads[: d // 4] = heads[0]          # duplicate heads
+        heads[-1] = v                       # self-loop
+        src.append(np.full(d, v))
+        dst.append(heads)
+    src.append(rng.integers(0, 600, 9000))  # the neighbourhood links back into itself
+    dst.append(rng.integers(0, 600, 9000))
+    src.append(rng.integers(600, n - 50, 20000))
+    dst.append(rng.integers(0, n, 20000))
+    g = gen.csr_raw(n, np.concatenate(src), np.concatenate(dst))
+    seeds = np.array([0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 7, 500, n - 1, 5999, 42], np.uint32)
+    ks = np.array([2, 2, 2, 2, 2, 3, 3, 6, 6, 3, 2, 2, 2, 2, 6], np.uint32)
+    check_graph(g, seeds, ks, hop=True)
+    check_graph(g, seeds, ks, hop=True, wide=True)
+
+
 def test_edge_cases_seed_out_of_range_and_k0():
     g = gen.rmat(8, 8, seed=1)
     G = kh.Graph.from_csr(g)
