@@ -113,6 +113,7 @@ struct Shared {
     int qfull;                   // this CTA saw the queue past its cap (pull rounds)
     unsigned long long slot[4];  // counters of the round just finished
     unsigned m1;                 // fused round: distinct out-neighbours of the seed
+    uint64_t ring_q;             // thread 0: the query whose ring_advance is due next
     int flag;
 };
 
@@ -645,9 +646,9 @@ __device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V,
     for (uint64_t i = gtid; i < a.nw; i += gthreads) V[i] = i == sw ? sb : 0u;
 }
 
-// Look-ahead over the query list for the one-CTA path: the heads of the next
-// queries, fetched by thread 0 with asynchronous copies into a shared-memory
-// ring, so no thread waits on the dependent loads seeds[i] -> rp[seed].  Each
+// Look-ahead over the query list: the heads of the next queries, fetched by
+// thread 0 of each CTA with asynchronous copies into a shared-memory ring, so
+// no thread waits on the dependent loads seeds[i] -> rp[seed].  Each
 // query start commits two copy groups -- the row bounds of q + 4 and the seed
 // and k of q + 6 -- and waits only for the groups of two query starts ago, so
 // every copy has two queries' time to land.  After ring_advance(q) the heads
@@ -765,7 +766,7 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
     const int lane = threadIdx.x & 31;
     const uint32_t s_first = cur.s;
     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) tab[i] = kHashEmpty;
-    if (threadIdx.x == 0) ring_restart(a, ring, q);
+    if (threadIdx.x == 0 && sh.ring_q != q) ring_restart(a, ring, q);   // else still in step
     __syncthreads();
     for (uint64_t run = 1;; ++run) {
         if (threadIdx.x == 0) ring_advance(a, ring, q);
@@ -819,7 +820,7 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
         __syncthreads();   // the set is empty again before the next query's inserts
     }
     if (threadIdx.x == 0) {
-        cp_async_wait_all();
+        sh.ring_q = q;   // ready for q (its copies may still be in flight)
         // V for the grid's next query: its seed only
         V[s_first >> 5] = 0u;
         if (q < a.nq) V[cur.s >> 5] = 1u << (cur.s & 31);
@@ -843,7 +844,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     uint32_t *s_npos = s_nbr + kHashSlots;            //   and each key's first row position
     __shared__ Shared sh;
     __shared__ E s_winc[BLOCK], s_wpos[BLOCK];        // flattened pull scan, 32 per warp
-    __shared__ Peek<E> s_ring[kRing];                 // one-CTA look-ahead over the query list
+    __shared__ Peek<E> s_ring[kRing];                 // look-ahead over the query list
 
     const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
     const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -856,6 +857,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
     unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
+    if (threadIdx.x == 0) sh.ring_q = ~0ull;
     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
         s_nbr[i] = kHashEmpty;
         s_npos[i] = 0xffffffffu;
@@ -896,7 +898,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         const uint32_t k = cur.k;
         uint32_t *V = par ? a.V1 : a.V0;
         uint32_t *Vnext = par ? a.V0 : a.V1;
-        const uint64_t qn = skip_trivial(a, q + 1, false, t_prev, &nxt);   // next query (no writes)
+        // The next query from the look-ahead ring (no wait on its loads).
+        if (threadIdx.x == 0) {
+            if (sh.ring_q != q) ring_restart(a, s_ring, q);
+            ring_advance(a, s_ring, q);
+            sh.ring_q = q + 1;
+        }
+        __syncthreads();
+        const uint64_t qn = ring_next(a, s_ring, q, nxt);
         if (all_pull) {
             // Round 1 pulls from the bitmap {s}: set it up before the round.
             uint32_t *Fs = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
