@@ -384,22 +384,34 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
 // position in the seed's row (the same order in every CTA, so all CTAs cut
 // round 2's edge list the same way), their row starts into s_rs and their
 // out-edge prefix sums into s_pre (s_pre[m1] = m_f of round 2).  `pos` holds
-// each key's first position.  Returns m1 (both tables are emptied by the
-// caller after the round).
+// each key's first position.  The row offsets of every position are loaded
+// alongside the inserts (a repeated head just loads its row twice), and one
+// scan over the threads -- which hold consecutive positions -- gives both each
+// kept head's index and its prefix.  Returns m1 (both tables are emptied by
+// the caller after the round).
 template <typename E, int BLOCK>
 __device__ __forceinline__ uint32_t fused_prelude(const PlainArgs<E> &a, uint32_t s, E rs0,
                                                   uint32_t deg, uint32_t *tab, uint32_t *pos, E *s_pre,
                                                   E *s_rs, Shared &sh) {
     constexpr int kPer = (int)(kFuseDeg / BLOCK);
-    uint32_t *ids = (uint32_t *)s_pre;   // the neighbours' ids, before the prefix sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ E s_wtot[32];
+    __shared__ unsigned long long s_wtot[32];   // per warp: kept count << 40 | edge sum
     // thread t holds row positions t * kPer .. t * kPer + kPer - 1
     uint32_t w[kPer], slot[kPer];
+    E rsv[kPer], rev[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const uint32_t e = threadIdx.x * kPer + u;
         w[u] = e < deg ? a.ci[(uint64_t)rs0 + e] : kHashEmpty;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        rsv[u] = 0;
+        rev[u] = 0;
+        if (w[u] != kHashEmpty) {
+            rsv[u] = a.rp[w[u]];
+            rev[u] = a.rp[w[u] + 1];
+        }
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
@@ -410,58 +422,35 @@ __device__ __forceinline__ uint32_t fused_prelude(const PlainArgs<E> &a, uint32_
         }
     }
     __syncthreads();
-    // keep each neighbour at its first position; compact in row order
+    // keep each neighbour at its first position: (count, edges) of this thread
     unsigned keep = 0;
+    unsigned long long mine = 0;
 #pragma unroll
     for (int u = 0; u < kPer; ++u)
-        if (slot[u] < kHashSlots && pos[slot[u]] == threadIdx.x * kPer + u) keep |= 1u << u;
-    const E kc = (E)__popc(keep);
-    E incl = warp_inclusive_sum(kc);
+        if (slot[u] < kHashSlots && pos[slot[u]] == threadIdx.x * kPer + u) {
+            keep |= 1u << u;
+            mine += (1ull << 40) + (unsigned long long)(rev[u] - rsv[u]);
+        }
+    const unsigned long long incl = warp_inclusive_sum(mine);
     if (lane == 31) s_wtot[warp] = incl;
     __syncthreads();
-    E base = incl - kc, tot = 0;
+    unsigned long long base = incl - mine, tot = 0;
     for (int i = 0; i < BLOCK / 32; ++i) {
         if (i < warp) base += s_wtot[i];
         tot += s_wtot[i];
     }
-    const uint32_t m1 = (uint32_t)tot;
+    uint32_t idx = (uint32_t)(base >> 40);
+    E pre = (E)(base & ((1ull << 40) - 1ull));
 #pragma unroll
     for (int u = 0; u < kPer; ++u)
-        if ((keep >> u) & 1u) ids[base++] = w[u];
-    __syncthreads();   // ids complete; s_wtot free again
-    // row bounds of the items this thread owns: [t * c, t * c + c)
-    const uint32_t c = (m1 + BLOCK - 1) / BLOCK;
-    const uint32_t i0 = min(threadIdx.x * c, m1), i1 = min(i0 + c, m1);
-    E rsv[kPer], dv[kPer];
-    E local = 0;
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        rsv[j] = 0;
-        dv[j] = 0;
-        if (i0 + j < i1) {
-            const uint32_t v = ids[i0 + j];
-            rsv[j] = a.rp[v];
-            dv[j] = a.rp[v + 1] - rsv[j];
+        if ((keep >> u) & 1u) {
+            s_pre[idx] = pre;
+            s_rs[idx] = rsv[u];
+            pre += rev[u] - rsv[u];
+            ++idx;
         }
-    }
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) local += dv[j];
-    // exclusive scan of the per-thread sums over the CTA
-    incl = warp_inclusive_sum(local);
-    if (lane == 31) s_wtot[warp] = incl;
-    __syncthreads();   // also: every thread has read its ids before s_pre is overwritten
-    E wbase = 0;
-    for (int i = 0; i < warp; ++i) wbase += s_wtot[i];
-    E pre = wbase + incl - local;
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        if (i0 + j < i1) {
-            s_pre[i0 + j] = pre;
-            s_rs[i0 + j] = rsv[j];
-            pre += dv[j];
-        }
-    }
-    if (threadIdx.x == BLOCK - 1) s_pre[m1] = pre;   // the last thread's end = the total
+    const uint32_t m1 = (uint32_t)(tot >> 40);
+    if (threadIdx.x == 0) s_pre[m1] = (E)(tot & ((1ull << 40) - 1ull));
     __syncthreads();
     return m1;
 }
