@@ -641,8 +641,8 @@ __device__ __forceinline__ void prep_visited(const PlainArgs<E> &a, uint32_t *V,
 // query start commits two copy groups -- the row bounds of q + 4 and the seed
 // and k of q + 6 -- and waits only for the groups of two query starts ago, so
 // every copy has two queries' time to land.  After ring_advance(q) the heads
-// of q + 1 and q + 2 are complete and the row of q + 2 is being prefetched
-// into L2 (at most kSoloEdges out-edges of it).
+// of q + 1 and q + 2 are complete; once published, other warps prefetch the
+// row of q + 2 into L2.
 template <typename E>
 struct Peek {
     uint32_t s, k;
@@ -678,12 +678,17 @@ __device__ __forceinline__ void ring_stage2(const PlainArgs<E> &a, Peek<E> *ring
     cp_async_commit();
 }
 
+// Warm L2 with the row of query i (at most kSoloEdges out-edges; its head must
+// be complete and published): thread t of nt takes every nt-th 128-byte line.
 template <typename E>
-__device__ __forceinline__ void ring_prefetch_row(const PlainArgs<E> &a, const Peek<E> *ring, uint64_t i) {
+__device__ __forceinline__ void ring_prefetch_row(const PlainArgs<E> &a, const Peek<E> *ring, uint64_t i,
+                                                  unsigned t, unsigned nt) {
     const Peek<E> &p = ring[i % kRing];
     if (i < a.nq && p.s < a.n && p.re > p.rs) {
         const uint64_t nd = min((uint64_t)(p.re - p.rs), (uint64_t)kSoloEdges);
-        for (uint64_t e = 0; e < nd; e += 128 / sizeof(uint32_t)) prefetch_l2(a.ci + (uint64_t)p.rs + e);
+        constexpr uint64_t kLine = 128 / sizeof(uint32_t);
+        for (uint64_t e = (uint64_t)t * kLine; e < nd; e += (uint64_t)nt * kLine)
+            prefetch_l2(a.ci + (uint64_t)p.rs + e);
     }
 }
 
@@ -693,7 +698,6 @@ __device__ __forceinline__ void ring_advance(const PlainArgs<E> &a, Peek<E> *rin
     cp_async_wait_group<2>();   // the groups of ring_advance(q - 2) and before
     ring_stage2(a, ring, q + 4);
     ring_stage1(a, ring, q + 6);
-    ring_prefetch_row(a, ring, q + 2);
 }
 
 // Thread 0: (re)start the ring in the state ring_advance(q) expects: heads of
@@ -705,7 +709,7 @@ __device__ __forceinline__ void ring_restart(const PlainArgs<E> &a, Peek<E> *rin
     cp_async_wait_all();
     for (uint64_t i = q + 1; i <= q + 3; ++i) ring_stage2(a, ring, i);
     cp_async_wait_all();
-    ring_prefetch_row(a, ring, q + 1);
+    ring_prefetch_row(a, ring, q + 1, 0u, 1u);
 }
 
 // The first query after q that needs a traversal (no writes), from the ring's
@@ -779,6 +783,7 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
         __syncthreads();   // counts complete; the ring's heads of q + 1, q + 2 published
         QueryHead<E> nxt{0u, 0u, (E)0, (E)0};
         const uint64_t qn = ring_next(a, ring, q, nxt);
+        if (threadIdx.x >= 32) ring_prefetch_row(a, ring, q + 2, threadIdx.x - 32u, BLOCK - 32u);
         if (threadIdx.x == 0) {
             const uint64_t cnt = sh.cnt;
             sh.cnt = 0;
@@ -895,6 +900,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         }
         __syncthreads();
         const uint64_t qn = ring_next(a, s_ring, q, nxt);
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x >= 32)
+            ring_prefetch_row(a, s_ring, q + 2, threadIdx.x - 32u, BLOCK - 32u);
         if (all_pull) {
             // Round 1 pulls from the bitmap {s}: set it up before the round.
             uint32_t *Fs = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
