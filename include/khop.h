@@ -68,18 +68,29 @@ enum khop_graph_flags {
     KHOP_SYMMETRIC = 2,     /* caller asserts A = A^T; the CSC is the CSR       */
     KHOP_VALIDATE = 4,      /* check the CSR (monotone row_ptr, row_ptr[n] =
                                nnz, col_idx < n) before use; EINVAL if not      */
-    KHOP_WIDE_OFFSETS = 8   /* keep 64-bit edge offsets on the device even when
+    KHOP_WIDE_OFFSETS = 8,  /* keep 64-bit edge offsets on the device even when
                                nnz < 2^32 (otherwise they are stored 32-bit)    */
+    KHOP_REVERSE = 16,      /* count in-neighbourhoods: q_r = A q_{r-1}, the
+                               frontier expands along edges backwards (the graph
+                               is stored transposed)                             */
+    KHOP_UNDIRECTED = 32    /* count along edges in either direction:
+                               q_r = (A OR A^T) q_{r-1}; the graph is stored as
+                               the union of each vertex's out- and in-list
+                               (2 nnz entries).  Overrides KHOP_REVERSE.         */
 };
 
 /*
  * Create a graph from CSR: row u lists the heads w of the edges u -> w (the
  * rows of the adjacency matrix A).  The transpose A^T (CSC, in-edges) is
- * derived on the device.
+ * derived on the device.  By default a query counts the out-neighbourhood
+ * (Sec. III: q_r = A^T q_{r-1}); KHOP_REVERSE and KHOP_UNDIRECTED select the
+ * in-neighbourhood and the either-direction neighbourhood, for every later
+ * count, batch and server request on the graph.
  *   n              vertices, 1 <= n < 2^32 (col_idx is 32-bit)
  *   row_ptr        n+1 offsets, each row_ptr_bytes wide (4 or 8)
  *   col_idx        nnz uint32 column indices, each < n
- *   nnz            row_ptr[n]; bitlen(n) + bitlen(nnz) must be <= 64
+ *   nnz            row_ptr[n]; bitlen(n) + bitlen(nnz) must be <= 64 (with
+ *                  KHOP_UNDIRECTED: bitlen(n) + bitlen(2 nnz) <= 64)
  *   flags          khop_graph_flags
  *   stream         stream for the upload and the derivation
  *   out            receives the graph handle
@@ -176,6 +187,25 @@ enum khop_mode {
  */
 int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
                      uint64_t nseeds, uint64_t *out_counts, int mode, void *stream);
+
+/*
+ * The k-hop neighbourhood itself -- the visited set v_k of Sec. III, the seed
+ * included -- rather than its size, for one query on the plain path.
+ *   khop_neighbourhood: bit v of out_bits (ceil(n/32) uint32 words, device
+ *     memory, written whole) is set iff v is within k hops of `seed`;
+ *     out_count (device uint64, may be NULL) receives the count
+ *     (popcount - 1), as khop_count would.
+ *   khop_neighbourhood_list: the same set as vertex ids in ascending order:
+ *     the first min(size, capacity) ids go to out_ids (device uint32; may be
+ *     NULL when capacity is 0) and the set's size to *out_size (device
+ *     uint64), so a call with capacity 0 sizes the buffer for a second call.
+ * Asynchronous on `stream` like khop_count; ordered with the graph's other
+ * calls.  Errors: EINVAL (NULL graph or output, seed >= n), ECUDA.
+ */
+int khop_neighbourhood(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *out_bits,
+                       uint64_t *out_count, void *stream);
+int khop_neighbourhood_list(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *out_ids,
+                            uint64_t capacity, uint64_t *out_size, void *stream);
 
 /*
  * Counters of the last batched (KHOP_MODE_BATCHED64) launch on g: 64-lane

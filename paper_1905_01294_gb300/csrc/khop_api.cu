@@ -7,7 +7,135 @@
 
 using namespace khop;
 
+namespace {
+
+// The single query (seed, k) of a neighbourhood call, in device memory.
+__global__ void one_query_kernel(uint32_t *q, uint32_t seed, uint32_t k) {
+    q[0] = seed;
+    q[1] = k;
+}
+
+// The seed is in its own neighbourhood (also when the query needed no traversal).
+__global__ void seed_bit_kernel(uint32_t *bits, uint32_t seed) {
+    atomicOr(&bits[seed >> 5], 1u << (seed & 31));
+}
+
+// Vertex list from a bitmap, ascending: every block takes a contiguous run of
+// words; cnt[b] = bits in block b's run.
+__global__ void count_bits_kernel(const uint32_t *bits, uint64_t nw, uint64_t per_block, uint32_t *cnt) {
+    __shared__ unsigned s[32];
+    const uint64_t w0 = (uint64_t)blockIdx.x * per_block, w1 = min(w0 + per_block, nw);
+    unsigned c = 0;
+    for (uint64_t i = w0 + threadIdx.x; i < w1; i += blockDim.x) c += (unsigned)__popc(bits[i]);
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (unsigned i = 0; i < blockDim.x / 32; ++i) t += s[i];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// Writes the ids of block b's run at offset sum(cnt[0..b)); ids beyond
+// `capacity` are dropped; block 0 writes the total to *size.  One thread per
+// word, words in order.
+__global__ void write_ids_kernel(const uint32_t *bits, uint64_t nw, uint64_t per_block, const uint32_t *cnt,
+                                 uint32_t *ids, uint64_t capacity, uint64_t *size) {
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_warp[32];
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0, t = 0;
+        for (unsigned i = 0; i < gridDim.x; ++i) {
+            if (i < blockIdx.x) b += cnt[i];
+            t += cnt[i];
+        }
+        s_base = b;
+        if (blockIdx.x == 0) *size = t;
+    }
+    __syncthreads();
+    const uint64_t w0 = (uint64_t)blockIdx.x * per_block, w1 = min(w0 + per_block, nw);
+    unsigned long long base = s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t c0 = w0; c0 < w1; c0 += blockDim.x) {
+        const uint64_t i = c0 + threadIdx.x;
+        const uint32_t x = i < w1 ? bits[i] : 0u;
+        const unsigned c = (unsigned)__popc(x);
+        const unsigned incl = warp_inclusive_sum(c);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        unsigned before = incl - c, total = 0;
+        for (unsigned j = 0; j < blockDim.x / 32; ++j) {
+            if (j < (unsigned)warp) before += s_warp[j];
+            total += s_warp[j];
+        }
+        unsigned long long o = base + before;
+        for (uint32_t y = x; y; y &= y - 1, ++o)
+            if (o < capacity) ids[o] = (uint32_t)((i << 5) + (uint64_t)__ffs(y) - 1);
+        base += total;
+        __syncthreads();
+    }
+}
+
+// Runs the single query (seed, k) with every round on the grid path; the
+// neighbourhood is then plain.V (plus the seed bit).
+int run_one(khop_graph *g, uint32_t seed, uint32_t k, cudaStream_t st) {
+    uint32_t *q = g->plain.ctl->one_q;
+    one_query_kernel<<<1, 1, 0, st>>>(q, seed, k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = plain_launch(g, q, q + 1, 0, 1, (uint64_t *)&g->plain.ctl->one_out, nullptr, nullptr, nullptr, 0,
+                          st, true);
+    if (rc != KHOP_OK) return rc;
+    seed_bit_kernel<<<1, 1, 0, st>>>(g->plain.V, seed);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
 extern "C" {
+
+int khop_neighbourhood(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *out_bits, uint64_t *out_count,
+                       void *stream) {
+    if (!g || !out_bits || seed >= g->n) return KHOP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = order_after_previous(g, st);
+    if (rc == KHOP_OK) rc = run_one(g, seed, k, st);
+    if (rc == KHOP_OK)
+        rc = cuda_status(cudaMemcpyAsync(out_bits, g->plain.V, (uint64_t)g->nw * 4, cudaMemcpyDeviceToDevice, st));
+    if (rc == KHOP_OK && out_count)
+        rc = cuda_status(cudaMemcpyAsync(out_count, &g->plain.ctl->one_out, 8, cudaMemcpyDeviceToDevice, st));
+    if (rc == KHOP_OK) rc = mark_done(g, st);
+    return rc;
+}
+
+int khop_neighbourhood_list(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *out_ids, uint64_t capacity,
+                            uint64_t *out_size, void *stream) {
+    if (!g || !out_size || (capacity && !out_ids) || seed >= g->n) return KHOP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = order_after_previous(g, st);
+    if (rc == KHOP_OK) rc = run_one(g, seed, k, st);
+    if (rc == KHOP_OK) {
+        // the frontier bitmaps are free after the launch (the next one zeroes them)
+        const uint64_t nw = g->nw;
+        const uint64_t blocks = std::min<uint64_t>((uint64_t)g->num_sms * 4, nw);
+        const uint64_t per_block = (nw + blocks - 1) / blocks;
+        const uint64_t used = (nw + per_block - 1) / per_block;
+        uint32_t *cnt = g->plain.F[0];
+        count_bits_kernel<<<(unsigned)used, 256, 0, st>>>(g->plain.V, nw, per_block, cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            write_ids_kernel<<<(unsigned)used, 256, 0, st>>>(g->plain.V, nw, per_block, cnt, out_ids, capacity,
+                                                              out_size);
+            e = cudaGetLastError();
+        }
+        rc = cuda_status(e);
+    }
+    if (rc == KHOP_OK) rc = mark_done(g, st);
+    return rc;
+}
 
 int khop_count_ex(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nseeds,
                   uint64_t *out_counts, uint64_t *out_te, khop_query_stats *out_stats,

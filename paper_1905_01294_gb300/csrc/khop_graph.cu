@@ -224,6 +224,25 @@ __global__ void noin_kernel(const E *cp, uint64_t n, uint32_t nw, uint32_t *noin
     }
 }
 
+// Either-direction adjacency: row u of the result is out(u) followed by in(u).
+// ro[u] = rp[u] + cp[u] (both are prefix sums).  One warp per vertex.
+template <typename E, typename EO>
+__global__ void union_rows_kernel(const E *rp, const uint32_t *ci, const E *cp, const uint32_t *ri,
+                                  uint64_t n, EO *ro, uint32_t *co) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t u = warp; u <= n; u += nwarps) {
+        const EO base = (EO)rp[u] + (EO)cp[u];
+        if (lane == 0) ro[u] = base;
+        if (u == n) break;
+        const E o0 = rp[u], o1 = rp[u + 1], i0 = cp[u], i1 = cp[u + 1];
+        for (E x = o0 + lane; x < o1; x += 32) co[(uint64_t)base + (x - o0)] = ci[x];
+        const EO b2 = base + (EO)(o1 - o0);
+        for (E x = i0 + lane; x < i1; x += 32) co[(uint64_t)b2 + (x - i0)] = ri[x];
+    }
+}
+
 template <typename T>
 cudaError_t dalloc(khop_graph *g, T **p, uint64_t count) {
     const size_t bytes = std::max<uint64_t>(count, 1) * sizeof(T);
@@ -435,9 +454,13 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
     if (n == 0 || n >= (1ull << 32) || !row_ptr || (nnz && !col_idx)) return KHOP_EINVAL;
     if (row_ptr_bytes != 4 && row_ptr_bytes != 8) return KHOP_EINVAL;
     if (row_ptr_bytes == 4 && nnz >= (1ull << 32)) return KHOP_EINVAL;
-    if (flags & ~(uint32_t)(KHOP_DEVICE_PTRS | KHOP_SYMMETRIC | KHOP_VALIDATE | KHOP_WIDE_OFFSETS))
+    if (flags & ~(uint32_t)(KHOP_DEVICE_PTRS | KHOP_SYMMETRIC | KHOP_VALIDATE | KHOP_WIDE_OFFSETS |
+                            KHOP_REVERSE | KHOP_UNDIRECTED))
         return KHOP_EINVAL;
     if (bitlen(n) + bitlen(nnz) > 64) return KHOP_EINVAL;
+    const bool undirected = (flags & KHOP_UNDIRECTED) && !(flags & KHOP_SYMMETRIC);
+    const bool reverse = (flags & KHOP_REVERSE) && !(flags & (KHOP_SYMMETRIC | KHOP_UNDIRECTED));
+    if (undirected && bitlen(n) + bitlen(2 * nnz) > 64) return KHOP_EINVAL;
     const bool on_device = flags & KHOP_DEVICE_PTRS;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -524,10 +547,60 @@ int khop_graph_create(uint64_t n, const void *row_ptr, int row_ptr_bytes, const 
     } else {
         e = g->ewidth == 4 ? build_csc<uint32_t>(g, st) : build_csc<unsigned long long>(g, st);
         if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
+        if (undirected) {
+            // A OR A^T: each row is the out-list then the in-list; the result is
+            // its own transpose.
+            const uint64_t nnz2 = 2 * nnz;
+            const int ew2 = (nnz2 < (1ull << 32) && !(flags & KHOP_WIDE_OFFSETS)) ? 4 : 8;
+            void *ro = nullptr;
+            uint32_t *co = nullptr;
+            e = dalloc_raw(g, &ro, (n + 1) * (uint64_t)ew2);
+            if (e == cudaSuccess) e = dalloc(g, &co, nnz2);
+            if (e == cudaSuccess) {
+                if (g->ewidth == 4 && ew2 == 4)
+                    union_rows_kernel<uint32_t, uint32_t><<<blocks, 256, 0, st>>>(
+                        (const uint32_t *)g->rp, g->ci, (const uint32_t *)g->cp, g->ri, n, (uint32_t *)ro, co);
+                else if (g->ewidth == 4)
+                    union_rows_kernel<uint32_t, unsigned long long><<<blocks, 256, 0, st>>>(
+                        (const uint32_t *)g->rp, g->ci, (const uint32_t *)g->cp, g->ri, n,
+                        (unsigned long long *)ro, co);
+                else
+                    union_rows_kernel<unsigned long long, unsigned long long><<<blocks, 256, 0, st>>>(
+                        (const unsigned long long *)g->rp, g->ci, (const unsigned long long *)g->cp, g->ri, n,
+                        (unsigned long long *)ro, co);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { cudaFree(ro); cudaFree(co); free_graph(g); return cuda_status(e); }
+            const uint64_t W = (uint64_t)g->ewidth;
+            cudaFree(g->rp);
+            cudaFree(g->ci);
+            cudaFree(g->cp);
+            cudaFree(g->ri);
+            g->device_bytes -= 2 * ((n + 1) * W + std::max<uint64_t>(nnz, 1) * sizeof(uint32_t));
+            g->rp = ro;
+            g->ci = co;
+            g->cp = ro;
+            g->ri = co;
+            g->nnz = nnz2;
+            g->ewidth = ew2;
+            g->ebits = (uint32_t)(64 - bitlen(n));
+            g->symmetric = true;
+            e = g->ewidth == 4 ? order_inlists<uint32_t>(g, (const uint32_t *)g->rp, g->ci, st)
+                               : order_inlists<unsigned long long>(g, (const unsigned long long *)g->rp, g->ci, st);
+            if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
+        } else if (reverse) {
+            // in-neighbourhoods: traverse the transpose; its own transpose is A
+            std::swap(g->rp, g->cp);
+            std::swap(g->ci, g->ri);
+            e = g->ewidth == 4 ? order_inlists<uint32_t>(g, (const uint32_t *)g->cp, g->ri, st)
+                               : order_inlists<unsigned long long>(g, (const unsigned long long *)g->cp, g->ri, st);
+            if (e != cudaSuccess) { free_graph(g); return cuda_status(e); }
+        }
     }
 
     // Plain traversal state and the in-edge-less vertex map.
-    g->tf_cap = nnz / 256 + 2;
+    g->tf_cap = g->nnz / 256 + 2;
     const uint64_t nw = g->nw;
     e = dalloc(g, &g->noin, nw);
     if (e == cudaSuccess) {

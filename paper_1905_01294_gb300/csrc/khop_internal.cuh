@@ -193,7 +193,9 @@ struct CtlBlock {
     unsigned err;                   // sticky khop_device_error bits
     unsigned dirty;                 // batched state may be dirty (a launch did not finish)
     unsigned long long rdone;       // batched: rounds run so far (frontier buffer rotation)
-    unsigned pad2[28];
+    uint32_t one_q[2];              // plain path: (seed, k) of a single-query call
+    unsigned long long one_out;     //   and its count
+    unsigned pad2[24];
 };
 
 // Plain single-query traversal state (one query at a time).
@@ -280,9 +282,12 @@ int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm
                      int *grid);
 
 // plain path (khop_plain.cu)
+// keep_visited: every query runs on the grid path, so that after a launch of
+// one query the visited bitmap plain.V holds its whole neighbourhood.
 int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
-                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st);
+                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st,
+                 bool keep_visited = false);
 // The same on a standalone state, with at most grid_ctas CTAs (0 = fill the GPU).
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                        uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st);

@@ -64,6 +64,7 @@ struct PlainArgs {
     uint64_t *per_hop;
     uint32_t hop_stride;
     int direction;
+    int keep_v;              // every query on the grid path (the visited bitmap is wanted)
     float alpha, beta;
     uint32_t tile_log2;
     uint32_t ebits;
@@ -565,7 +566,7 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
             const unsigned nm = __ballot_sync(FULL, found[j]);
             if (lane == 0) {
                 R.Fout[i] = nm;
-                if (nm) R.V[i] = Vw[j] | nm;
+                if (nm) atomicOr(&R.V[i], nm);   // V keeps traversal marks only (no in-edge-less bits)
             }
             const uint64_t v = (i << 5) + (uint64_t)lane;
             E rs = 0, d = 0;
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
     unsigned par = 0;     // which visited bitmap the current query uses
     while (q < a.nq) {
-        if (solo_query(cur, all_pull)) {
+        if (!a.keep_v && solo_query(cur, all_pull)) {
             if (blockIdx.x == 0)
                 solo_run<E, BLOCK>(a, par ? a.V1 : a.V0, q, cur, t_prev, sh, s_ring, (uint32_t *)st_pre);
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, a.ctl->handoff, sh.slot, 4,
@@ -1110,7 +1111,7 @@ template <typename E>
 int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                  uint32_t k_all, uint64_t nq, uint64_t *out, uint64_t *out_te,
                  khop_query_stats *stats, uint64_t *per_hop, uint32_t hop_stride, int grid_ctas,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool keep_visited = false) {
     PlainArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -1144,6 +1145,7 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
     a.per_hop = per_hop;
     a.hop_stride = per_hop ? hop_stride : 0u;
     a.direction = g->tune.direction;
+    a.keep_v = keep_visited ? 1 : 0;
     a.alpha = g->tune.alpha;
     a.beta = g->tune.beta;
     uint32_t tl = 0;
@@ -1167,12 +1169,12 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
 
 int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
-                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st) {
+                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st, bool keep_visited) {
     if (g->ewidth == 4)
         return launch_typed<uint32_t>(g, g->plain, seeds, ks, k_all, nq, out, out_te, stats,
-                                      per_hop, hop_stride, 0, st);
+                                      per_hop, hop_stride, 0, st, keep_visited);
     return launch_typed<unsigned long long>(g, g->plain, seeds, ks, k_all, nq, out, out_te,
-                                            stats, per_hop, hop_stride, 0, st);
+                                            stats, per_hop, hop_stride, 0, st, keep_visited);
 }
 
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
@@ -1310,6 +1312,7 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     a.per_hop = nullptr;
     a.hop_stride = 0;
     a.direction = has_csc ? KHOP_DIR_AUTO : KHOP_DIR_PUSH;
+    a.keep_v = 0;
     a.alpha = 14.0f;
     a.beta = 24.0f;
     a.tile_log2 = 11;   // 2048-edge push tiles

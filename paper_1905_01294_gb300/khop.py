@@ -26,6 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, ESHUTDOWN, EDEVICE = range(8)
 DEVERR_TIMEOUT, DEVERR_SEED, DEVERR_CAPACITY = 1, 2, 4
 # graph flags
 HOST_PTRS, DEVICE_PTRS, SYMMETRIC, VALIDATE, WIDE_OFFSETS = 0, 1, 2, 4, 8
+REVERSE, UNDIRECTED = 16, 32
 # directions and modes
 DIR_AUTO, DIR_PUSH, DIR_PULL = 0, 1, 2
 MODE_AUTO, MODE_PLAIN, MODE_BATCHED64 = 0, 1, 2
@@ -37,7 +38,7 @@ EXPORTS = [
     "khop_graph_create", "khop_graph_destroy", "khop_graph_info", "khop_graph_device_bytes",
     "khop_graph_get_tuning", "khop_graph_set_tuning", "khop_autotune",
     "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
-    "khop_batch_stats",
+    "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list",
     "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
     "khop_server_destroy",
 ]
@@ -107,6 +108,8 @@ def lib():
                 "khop_count_ex": (i32, [vp, vp, vp, u64, vp, vp, vp, vp, u32, vp]),
                 "khop_count_static": (i32, [u64, vp, vp, vp, vp, u64, vp, u64, u32, vp, vp]),
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
+                "khop_neighbourhood": (i32, [vp, u32, u32, vp, vp, vp]),
+                "khop_neighbourhood_list": (i32, [vp, u32, u32, vp, u64, vp, vp]),
                 "khop_batch_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]),
                 "khop_server_create": (i32, [ctypes.POINTER(khop_server_opts), ctypes.POINTER(vp)]),
@@ -203,6 +206,15 @@ def khop_count_static(n, row_ptr, col_idx, col_ptr, row_idx, nnz, seeds, nseeds,
                                   out_counts, stream), "khop_count_static")
 
 
+def khop_neighbourhood(g, seed, k, out_bits, out_count, stream) -> None:
+    check(lib().khop_neighbourhood(g, seed, k, out_bits, out_count, stream), "khop_neighbourhood")
+
+
+def khop_neighbourhood_list(g, seed, k, out_ids, capacity, out_size, stream) -> None:
+    check(lib().khop_neighbourhood_list(g, seed, k, out_ids, capacity, out_size, stream),
+          "khop_neighbourhood_list")
+
+
 def khop_get_error(g) -> int:
     bits = ctypes.c_uint32()
     check(lib().khop_get_error(g, ctypes.byref(bits)), "khop_get_error")
@@ -280,13 +292,15 @@ class Graph:
     """A graph resident on the current CUDA device.
 
     row_ptr/col_idx: numpy arrays (host; copied) or CUDA torch tensors
-    (device; copied).  row_ptr may be 32- or 64-bit."""
+    (device; copied).  row_ptr may be 32- or 64-bit.  reverse: count
+    in-neighbourhoods; undirected: count along edges in either direction."""
 
     def __init__(self, n, row_ptr, col_idx, symmetric=False, validate=False, wide=False,
-                 stream=None):
+                 stream=None, reverse=False, undirected=False):
         torch = _torch()
         flags = ((SYMMETRIC if symmetric else 0) | (VALIDATE if validate else 0) |
-                 (WIDE_OFFSETS if wide else 0))
+                 (WIDE_OFFSETS if wide else 0) | (REVERSE if reverse else 0) |
+                 (UNDIRECTED if undirected else 0))
         if isinstance(row_ptr, np.ndarray):
             rp = np.ascontiguousarray(row_ptr)
             ci = np.ascontiguousarray(col_idx, dtype=np.uint32)
@@ -395,6 +409,33 @@ class Graph:
                       res["per_hop"].data_ptr() if hop_stride else None, hop_stride,
                       _stream_ptr(stream))
         return res
+
+    def neighbourhood(self, seed, k, stream=None):
+        """(bitmap, count): the k-hop neighbourhood of `seed` (seed included)
+        as ceil(n/32) int32 words on the device, and its count."""
+        torch = self._torch
+        nw = (self.n + 31) // 32
+        bits = torch.empty(nw, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+        khop_neighbourhood(self.handle, int(seed), int(k), bits.data_ptr(), cnt.data_ptr(),
+                           _stream_ptr(stream))
+        return bits, cnt
+
+    def neighbourhood_list(self, seed, k, capacity=None, stream=None):
+        """The k-hop neighbourhood of `seed` (seed included) as ascending
+        vertex ids (int32 tensor on the device).  Without a capacity, a first
+        call sizes the output."""
+        torch = self._torch
+        size = torch.zeros(1, dtype=torch.int64, device="cuda")
+        if capacity is None:
+            khop_neighbourhood_list(self.handle, int(seed), int(k), None, 0, size.data_ptr(),
+                                    _stream_ptr(stream))
+            torch.cuda.synchronize()
+            capacity = int(size.item())
+        ids = torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda")
+        khop_neighbourhood_list(self.handle, int(seed), int(k), ids.data_ptr(), capacity,
+                                size.data_ptr(), _stream_ptr(stream))
+        return ids[:capacity], size
 
     def autotune(self, seeds, k=None, ks=None, stream=None) -> khop_tuning:
         """Tune on these seeds with one k for all, or per-seed ks."""
