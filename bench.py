@@ -412,6 +412,76 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
             "sweep": points}
 
 
+def variants_leg(kh, torch, dev, stream, scale, steps, warmup, flush):
+    """The paper protocol (300/300/10/10 seeds at k = 1/2/3/6) on the directed
+    scale-`scale` R-MAT graph (edges kept one-way) counted along out-edges
+    (Sec. III's A^T q), in-edges (A q) and both (A OR A^T); default tuning,
+    one plain launch per step, L2 flushed between steps."""
+    g = gen.rmat(scale, 16, seed=1)
+    seeds, ks = paper_queries(g)
+    nq = seeds.size
+    d_seeds = torch.from_numpy(seeds.view(np.int32)).to(dev)
+    d_ks = torch.from_numpy(ks.view(np.int32)).to(dev)
+    d_out = torch.empty(nq, dtype=torch.int64, device=dev)
+    res = {"workload": f"kronecker-s{scale}-ef16 directed (nnz {g.nnz}), 620 paper-protocol queries, "
+                       "default tuning", "unit": "queries/s"}
+    for name, kw in (("out", {}), ("in", {"reverse": True}), ("either", {"undirected": True})):
+        Gv = kh.Graph.from_csr(g, **kw)
+
+        def step():
+            kh.khop_count_mixed(Gv.handle, d_seeds.data_ptr(), d_ks.data_ptr(), nq, d_out.data_ptr(),
+                                kh.MODE_PLAIN, stream.cuda_stream)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        counts = kh.as_u64(d_out)
+        res[name] = {"value": nq * steps / (ms * 1e-3), "mean_count": float(counts.mean()),
+                     "ms_per_step": ms / steps}
+        Gv.close()
+    return res
+
+
+def listing_leg(kh, torch, G, g, seeds, ks, counts, dev, stream):
+    """The neighbourhoods themselves (khop_neighbourhood_list: ascending ids)
+    for the paper protocol's distinct (seed, k) pairs at k = 2, 3, 6 (the
+    first 50 at k = 2): sets/s and ids/s over one call each, every size
+    checked against the plain count."""
+    ids = torch.empty(g.n, dtype=torch.int32, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    pick = [i for i in range(seeds.size) if ks[i] in (3, 6)] + \
+        [i for i in range(seeds.size) if ks[i] == 2][:50]
+    for i in pick[:3]:   # warm-up
+        kh.khop_neighbourhood_list(G.handle, int(seeds[i]), int(ks[i]), ids.data_ptr(), g.n,
+                                   size.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms, total = 0.0, 0
+    for i in pick:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kh.khop_neighbourhood_list(G.handle, int(seeds[i]), int(ks[i]), ids.data_ptr(), g.n,
+                                   size.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        sz = int(size.item())
+        if sz != int(counts[i]) + 1:
+            raise SystemExit("neighbourhood size differs from the count")
+        total += sz
+    return {"workload": f"{len(pick)} paper-protocol (seed, k) pairs at k = 2/3/6, one call each",
+            "value": len(pick) / (ms * 1e-3), "unit": "sets/s", "ids_per_s": total / (ms * 1e-3),
+            "mean_size": total / len(pick)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,6 +625,10 @@ def main():
     if not args.no_extras:
         extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
                                         flush, peak, nq=batched_nq, gname=wname.split(" ")[0])
+        extras["listing"] = listing_leg(kh, torch, G, g, seeds, ks, ref_counts, dev, stream)
+        if args.workload == "kronecker21":
+            extras["directions"] = variants_leg(kh, torch, dev, stream, args.scale, args.steps,
+                                                args.warmup, flush)
         if not args.no_serving:
             mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
             if args.workload == "chunglu":
