@@ -453,9 +453,10 @@ def variants_leg(kh, torch, dev, stream, scale, steps, warmup, flush):
 
 def listing_leg(kh, torch, G, g, seeds, ks, counts, dev, stream):
     """The neighbourhoods themselves (khop_neighbourhood_list: ascending ids)
-    for the paper protocol's distinct (seed, k) pairs at k = 2, 3, 6 (the
-    first 50 at k = 2): sets/s and ids/s over one call each, every size
-    checked against the plain count."""
+    for the paper protocol's (seed, k) pairs at k = 3, 6 and the first 50 at
+    k = 2: sets/s and ids/s over one call each, every size checked against
+    the plain count; then khop_levels (hop levels and (MIN, SECOND) parents
+    of all n vertices) for the same pairs."""
     ids = torch.empty(g.n, dtype=torch.int32, device=dev)
     size = torch.zeros(1, dtype=torch.int64, device=dev)
     pick = [i for i in range(seeds.size) if ks[i] in (3, 6)] + \
@@ -477,9 +478,21 @@ def listing_leg(kh, torch, G, g, seeds, ks, counts, dev, stream):
         if sz != int(counts[i]) + 1:
             raise SystemExit("neighbourhood size differs from the count")
         total += sz
+    # BFS levels and (MIN, SECOND) parents of the same pairs (khop_levels)
+    lv = torch.empty(g.n, dtype=torch.int32, device=dev)
+    par = torch.empty(g.n, dtype=torch.int32, device=dev)
+    ms_l = 0.0
+    for i in pick:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kh.khop_levels(G.handle, int(seeds[i]), int(ks[i]), lv.data_ptr(), par.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms_l += a.elapsed_time(b)
     return {"workload": f"{len(pick)} paper-protocol (seed, k) pairs at k = 2/3/6, one call each",
             "value": len(pick) / (ms * 1e-3), "unit": "sets/s", "ids_per_s": total / (ms * 1e-3),
-            "mean_size": total / len(pick)}
+            "mean_size": total / len(pick),
+            "levels_and_parents_per_s": len(pick) / (ms_l * 1e-3)}
 
 
 def main():

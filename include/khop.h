@@ -189,6 +189,22 @@ int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks,
                      uint64_t nseeds, uint64_t *out_counts, int mode, void *stream);
 
 /*
+ * Hop levels of one query's BFS (Sec. III's rounds as the (MIN, +) semiring)
+ * and, optionally, BFS parents over the (MIN, SECOND) semiring.
+ *   out_levels   device int32[n]: level(v) = hop distance from `seed` if it
+ *                is <= k (0 for the seed), else -1
+ *   out_parents  device uint32[n] or NULL: parent(v) = the smallest
+ *                in-neighbour u of v with level(u) = level(v) - 1 for a
+ *                reached v != seed; parent(seed) = seed; UINT32_MAX for
+ *                unreached vertices.  Unique, so any correct BFS gives it.
+ * On a KHOP_REVERSE / KHOP_UNDIRECTED graph "in-neighbour" follows the
+ * traversal direction.  Asynchronous on `stream`, ordered with the graph's
+ * other calls.  Errors: EINVAL (NULL graph or out_levels, seed >= n), ECUDA.
+ */
+int khop_levels(khop_graph *g, uint32_t seed, uint32_t k, int32_t *out_levels,
+                uint32_t *out_parents, void *stream);
+
+/*
  * The k-hop neighbourhood itself -- the visited set v_k of Sec. III, the seed
  * included -- rather than its size, for one query on the plain path.
  *   khop_neighbourhood: bit v of out_bits (ceil(n/32) uint32 words, device

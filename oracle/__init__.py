@@ -99,3 +99,20 @@ def khop_dist(g, s: int, k: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("seed out of range" if rc == -1 else "oracle out of memory")
     return out
+
+
+def bfs_parents(g, s: int, k: int) -> np.ndarray:
+    """uint32 BFS parents over the (MIN, SECOND) semiring, from the hop
+    distances (Sec. II's semiring view of a traversal; parent = the smallest
+    predecessor one hop closer): parent[v] = min{u : u -> v, dist(u) =
+    dist(v) - 1} for 1 <= dist(v) <= k, parent[s] = s, UINT32_MAX elsewhere.
+    The definition written out over every edge."""
+    d = khop_dist(g, s, k)
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(rp))
+    dst = np.asarray(g.col_idx[: int(rp[-1])], dtype=np.int64)
+    ok = (d[src] >= 0) & (d[dst] == d[src] + 1)
+    par = np.full(g.n, np.iinfo(np.uint32).max, dtype=np.uint64)
+    np.minimum.at(par, dst[ok], src[ok].astype(np.uint64))
+    par[s] = s
+    return par.astype(np.uint32)

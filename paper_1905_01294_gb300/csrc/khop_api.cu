@@ -78,17 +78,46 @@ __global__ void write_ids_kernel(const uint32_t *bits, uint64_t nw, uint64_t per
 }
 
 // Runs the single query (seed, k) with every round on the grid path; the
-// neighbourhood is then plain.V (plus the seed bit).
-int run_one(khop_graph *g, uint32_t seed, uint32_t k, cudaStream_t st) {
+// neighbourhood is then plain.V (plus the seed bit); levels, if given, get
+// the hop distance of every vertex the rounds discover.
+int run_one(khop_graph *g, uint32_t seed, uint32_t k, cudaStream_t st, int32_t *levels = nullptr) {
     uint32_t *q = g->plain.ctl->one_q;
     one_query_kernel<<<1, 1, 0, st>>>(q, seed, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     int rc = plain_launch(g, q, q + 1, 0, 1, (uint64_t *)&g->plain.ctl->one_out, nullptr, nullptr, nullptr, 0,
-                          st, true);
+                          st, true, levels);
     if (rc != KHOP_OK) return rc;
     seed_bit_kernel<<<1, 1, 0, st>>>(g->plain.V, seed);
     return cuda_status(cudaGetLastError());
+}
+
+__global__ void seed_level_kernel(int32_t *levels, uint32_t seed) { levels[seed] = 0; }
+
+// BFS parents over the (MIN, SECOND) semiring: parent(v) = the smallest
+// in-neighbour u of v with level(u) = level(v) - 1 (v reached, v != s);
+// parent(s) = s; unreached vertices get UINT32_MAX.  One warp per vertex
+// over its in-list.
+template <typename E>
+__global__ void parents_kernel(const E *cp, const uint32_t *ri, const int32_t *levels, uint64_t n,
+                               uint32_t *parents) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t v = warp; v < n; v += nwarps) {
+        const int32_t lv = levels[v];
+        uint32_t best = 0xffffffffu;
+        if (lv > 0) {
+            for (E x = cp[v] + lane; x < cp[v + 1]; x += 32) {
+                const uint32_t u = ri[x];
+                if (levels[u] == lv - 1) best = min(best, u);
+            }
+            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL, best, o));
+        } else if (lv == 0) {
+            best = (uint32_t)v;
+        }
+        if (lane == 0) parents[v] = best;
+    }
 }
 
 }  // namespace
@@ -106,6 +135,32 @@ int khop_neighbourhood(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *out_b
         rc = cuda_status(cudaMemcpyAsync(out_bits, g->plain.V, (uint64_t)g->nw * 4, cudaMemcpyDeviceToDevice, st));
     if (rc == KHOP_OK && out_count)
         rc = cuda_status(cudaMemcpyAsync(out_count, &g->plain.ctl->one_out, 8, cudaMemcpyDeviceToDevice, st));
+    if (rc == KHOP_OK) rc = mark_done(g, st);
+    return rc;
+}
+
+int khop_levels(khop_graph *g, uint32_t seed, uint32_t k, int32_t *out_levels, uint32_t *out_parents,
+                void *stream) {
+    if (!g || !out_levels || seed >= g->n) return KHOP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = order_after_previous(g, st);
+    if (rc == KHOP_OK) rc = cuda_status(cudaMemsetAsync(out_levels, 0xff, g->n * sizeof(int32_t), st));
+    if (rc == KHOP_OK) rc = run_one(g, seed, k, st, out_levels);
+    if (rc == KHOP_OK) {
+        seed_level_kernel<<<1, 1, 0, st>>>(out_levels, seed);
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == KHOP_OK && out_parents) {
+        const int blocks = g->num_sms * 8;
+        if (g->ewidth == 4)
+            parents_kernel<uint32_t><<<blocks, 256, 0, st>>>((const uint32_t *)g->cp, g->ri, out_levels, g->n,
+                                                            out_parents);
+        else
+            parents_kernel<unsigned long long><<<blocks, 256, 0, st>>>((const unsigned long long *)g->cp, g->ri,
+                                                                      out_levels, g->n, out_parents);
+        rc = cuda_status(cudaGetLastError());
+    }
     if (rc == KHOP_OK) rc = mark_done(g, st);
     return rc;
 }

@@ -284,10 +284,11 @@ int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm
 // plain path (khop_plain.cu)
 // keep_visited: every query runs on the grid path, so that after a launch of
 // one query the visited bitmap plain.V holds its whole neighbourhood.
+// levels (or null): levels[w] = r for every w discovered in round r.
 int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
                  uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st,
-                 bool keep_visited = false);
+                 bool keep_visited = false, int32_t *levels = nullptr);
 // The same on a standalone state, with at most grid_ctas CTAs (0 = fill the GPU).
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                        uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st);

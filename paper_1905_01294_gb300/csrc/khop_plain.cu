@@ -65,6 +65,7 @@ struct PlainArgs {
     uint32_t hop_stride;
     int direction;
     int keep_v;              // every query on the grid path (the visited bitmap is wanted)
+    int32_t *levels;         // or null: levels[w] = r when round r discovers w
     float alpha, beta;
     uint32_t tile_log2;
     uint32_t ebits;
@@ -100,6 +101,7 @@ struct Round {
                              // out-neighbours) are in shared memory, and heads in that
                              // set (or the seed) are skipped
     const uint32_t *nbr;     // fused: hash set of the seed's distinct out-neighbours
+    uint32_t level;          // the round's number (its discoveries are at that hop distance)
 };
 
 // Per-CTA shared state of a round.
@@ -195,6 +197,7 @@ __device__ __forceinline__ void record(const PlainArgs<E> &a, const Round<E> &R,
                                        E *st_pre, E *st_rs, E *st_d) {
     const unsigned m = __ballot_sync(FULL, disc);
     if (m == 0u) return;
+    if (a.levels && disc) a.levels[w] = (int32_t)R.level;
     const int lane = threadIdx.x & 31;
     if (R.last) {
         if (lane == 0) atomicAdd(&sh.cnt, (unsigned long long)__popc(m));
@@ -959,7 +962,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                 if (fused && blockIdx.x == 0)   // q_1 visited (round 2 skips it)
                     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
                         const uint32_t x = s_nbr[i];
-                        if (x != kHashEmpty) atomicOr(&V[x >> 5], 1u << (x & 31));
+                        if (x != kHashEmpty) {
+                            atomicOr(&V[x >> 5], 1u << (x & 31));
+                            if (a.levels) a.levels[x] = 1;
+                        }
                     }
                 if (!fused) {
                     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
@@ -975,6 +981,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.precheck = mf > kPrecheckEdges && visited * 32 > a.n;
             R.fused = fused;
             R.nbr = s_nbr;
+            R.level = fused ? 2u : r;
             R.seed = s;
             R.seed_rs = cur.rs;
             R.V = V;
@@ -1111,7 +1118,7 @@ template <typename E>
 int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                  uint32_t k_all, uint64_t nq, uint64_t *out, uint64_t *out_te,
                  khop_query_stats *stats, uint64_t *per_hop, uint32_t hop_stride, int grid_ctas,
-                 cudaStream_t st, bool keep_visited = false) {
+                 cudaStream_t st, bool keep_visited = false, int32_t *levels = nullptr) {
     PlainArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -1145,7 +1152,8 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
     a.per_hop = per_hop;
     a.hop_stride = per_hop ? hop_stride : 0u;
     a.direction = g->tune.direction;
-    a.keep_v = keep_visited ? 1 : 0;
+    a.keep_v = keep_visited || levels ? 1 : 0;
+    a.levels = levels;
     a.alpha = g->tune.alpha;
     a.beta = g->tune.beta;
     uint32_t tl = 0;
@@ -1169,12 +1177,13 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
 
 int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint32_t k_all,
                  uint64_t nq, uint64_t *out, uint64_t *out_te, khop_query_stats *stats,
-                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st, bool keep_visited) {
+                 uint64_t *per_hop, uint32_t hop_stride, cudaStream_t st, bool keep_visited,
+                 int32_t *levels) {
     if (g->ewidth == 4)
         return launch_typed<uint32_t>(g, g->plain, seeds, ks, k_all, nq, out, out_te, stats,
-                                      per_hop, hop_stride, 0, st, keep_visited);
+                                      per_hop, hop_stride, 0, st, keep_visited, levels);
     return launch_typed<unsigned long long>(g, g->plain, seeds, ks, k_all, nq, out, out_te,
-                                            stats, per_hop, hop_stride, 0, st, keep_visited);
+                                            stats, per_hop, hop_stride, 0, st, keep_visited, levels);
 }
 
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
@@ -1313,6 +1322,7 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     a.hop_stride = 0;
     a.direction = has_csc ? KHOP_DIR_AUTO : KHOP_DIR_PUSH;
     a.keep_v = 0;
+    a.levels = nullptr;
     a.alpha = 14.0f;
     a.beta = 24.0f;
     a.tile_log2 = 11;   // 2048-edge push tiles

@@ -38,7 +38,7 @@ EXPORTS = [
     "khop_graph_create", "khop_graph_destroy", "khop_graph_info", "khop_graph_device_bytes",
     "khop_graph_get_tuning", "khop_graph_set_tuning", "khop_autotune",
     "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
-    "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list",
+    "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list", "khop_levels",
     "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
     "khop_server_destroy",
 ]
@@ -110,6 +110,7 @@ def lib():
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
                 "khop_neighbourhood": (i32, [vp, u32, u32, vp, vp, vp]),
                 "khop_neighbourhood_list": (i32, [vp, u32, u32, vp, u64, vp, vp]),
+                "khop_levels": (i32, [vp, u32, u32, vp, vp, vp]),
                 "khop_batch_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]),
                 "khop_server_create": (i32, [ctypes.POINTER(khop_server_opts), ctypes.POINTER(vp)]),
@@ -213,6 +214,10 @@ def khop_neighbourhood(g, seed, k, out_bits, out_count, stream) -> None:
 def khop_neighbourhood_list(g, seed, k, out_ids, capacity, out_size, stream) -> None:
     check(lib().khop_neighbourhood_list(g, seed, k, out_ids, capacity, out_size, stream),
           "khop_neighbourhood_list")
+
+
+def khop_levels(g, seed, k, out_levels, out_parents, stream) -> None:
+    check(lib().khop_levels(g, seed, k, out_levels, out_parents, stream), "khop_levels")
 
 
 def khop_get_error(g) -> int:
@@ -436,6 +441,16 @@ class Graph:
         khop_neighbourhood_list(self.handle, int(seed), int(k), ids.data_ptr(), capacity,
                                 size.data_ptr(), _stream_ptr(stream))
         return ids[:capacity], size
+
+    def levels(self, seed, k, parents=True, stream=None):
+        """(levels, parents): int32 hop levels (-1 beyond k) and, if asked,
+        the (MIN, SECOND) BFS parents (int32 view of uint32; -1 unreached)."""
+        torch = self._torch
+        lv = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        par = torch.empty(self.n, dtype=torch.int32, device="cuda") if parents else None
+        khop_levels(self.handle, int(seed), int(k), lv.data_ptr(),
+                    par.data_ptr() if parents else None, _stream_ptr(stream))
+        return lv, par
 
     def autotune(self, seeds, k=None, ks=None, stream=None) -> khop_tuning:
         """Tune on these seeds with one k for all, or per-seed ks."""

@@ -284,3 +284,43 @@ def test_planted_mistakes_are_caught(mi, monkeypatch, tmp_path):
         except AssertionError:
             failed += 1
     assert failed > 0
+
+
+# ---- BFS levels and (MIN, SECOND) parents -----------------------------------
+
+def test_parents_on_path_star_and_diamond():
+    p = oracle.bfs_parents(gen.path_graph(8), 2, 3)
+    assert p[2] == 2 and list(p[3:6]) == [2, 3, 4]
+    assert (p[[0, 1, 6, 7]] == 0xFFFFFFFF).all()       # behind the seed, beyond k
+    st = gen.out_star(6)
+    assert (oracle.bfs_parents(st, 0, 1)[1:] == 0).all()
+    # diamond 0->1, 0->2, 1->3, 2->3, 2->4: vertex 3 has two predecessors -> the smaller
+    d = gen.csr_raw(5, [0, 0, 1, 2, 2], [1, 2, 3, 3, 4])
+    assert list(oracle.bfs_parents(d, 0, 2)) == [0, 0, 0, 1, 2]
+    assert list(oracle.bfs_parents(d, 0, 1)) == [0, 0, 0, 0xFFFFFFFF, 0xFFFFFFFF]
+
+
+def test_levels_and_parents_against_networkx_bfs():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(17)
+    for _ in range(20):
+        n = int(rng.integers(2, 60))
+        m = int(rng.integers(0, 4 * n))
+        src, dst = rng.integers(0, n, m), rng.integers(0, n, m)
+        g = gen.csr_raw(n, src, dst)
+        G = nx.DiGraph()
+        G.add_nodes_from(range(n))
+        G.add_edges_from(zip(src.tolist(), dst.tolist()))
+        s, k = int(rng.integers(0, n)), int(rng.integers(0, 6))
+        ref = nx.single_source_shortest_path_length(G, s, cutoff=k)
+        d = oracle.khop_dist(g, s, k)
+        assert {v: int(x) for v, x in enumerate(d) if x >= 0} == ref
+        par = oracle.bfs_parents(g, s, k)
+        for v in range(n):
+            if v == s:
+                assert par[v] == s
+            elif v in ref:
+                preds = [u for u in G.predecessors(v) if ref.get(u, -9) == ref[v] - 1]
+                assert par[v] == min(preds)
+            else:
+                assert par[v] == 0xFFFFFFFF
