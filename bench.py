@@ -315,6 +315,24 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
     te = int(kh.as_u64(d_te).sum())
     t = sum(ms) * 1e-3
     achieved = byts / t / 1e9
+    # the same queries 128 per traversal (two lane words per vertex), same tuning
+    kh.khop_count_mixed(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_o.data_ptr(),
+                        kh.MODE_BATCHED128, stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms128 = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kh.khop_count_mixed(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_o.data_ptr(),
+                            kh.MODE_BATCHED128, stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms128.append(a.elapsed_time(b))
+    if not np.array_equal(got, kh.as_u64(d_o)):
+        raise SystemExit("128-lane counts differ from the 64-lane ones")
+    lanes128 = {"value": nq * steps / (sum(ms128) * 1e-3), "unit": "queries/s",
+                "ms_per_step": float(np.mean(ms128)), "mode": "KHOP_MODE_BATCHED128 (direct calls)"}
     return {"workload": f"{gname}, {nq} seeds (seed 2), k uniform over {{1,2,3,6}}, "
                         "64 queries per uint64 lane word, persistent launch replayed from a "
                         "captured CUDA graph",
@@ -327,7 +345,8 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
             "pull_rounds_per_step": st["pull_rounds"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": captured_traffic("batch_kernel"),
-                         "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"}}
+                         "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"},
+            "lanes128": lanes128}
 
 
 K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))

@@ -173,13 +173,15 @@ int khop_count(khop_graph *g, const uint32_t *seeds, uint64_t nseeds, uint32_t k
 enum khop_mode {
     KHOP_MODE_AUTO = 0,       /* batched for nseeds >= 2, else plain              */
     KHOP_MODE_PLAIN = 1,      /* one query at a time                              */
-    KHOP_MODE_BATCHED64 = 2   /* up to 64 queries share one bit-sliced traversal  */
+    KHOP_MODE_BATCHED64 = 2,  /* up to 64 queries share one bit-sliced traversal  */
+    KHOP_MODE_BATCHED128 = 3  /* up to 128 queries share one traversal (two lane
+                                 words per vertex)                              */
 };
 
 /*
  * Per-seed k (ks[i] for seeds[i]).  In KHOP_MODE_BATCHED64 the queries are
- * grouped by k and packed 64 per uint64 lane word; every lane's result equals
- * the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
+ * grouped by k and packed 64 per uint64 lane word (KHOP_MODE_BATCHED128: 128
+ * per pair of words); every lane's result equals the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
  * After a first call with the same mode on g (which allocates the batch
  * state), khop_count, khop_count_ex and khop_count_mixed issue only stream
  * work, so they may be captured into a CUDA graph and replayed; the graph
@@ -224,8 +226,7 @@ int khop_neighbourhood_list(khop_graph *g, uint32_t seed, uint32_t k, uint32_t *
                             uint64_t capacity, uint64_t *out_size, void *stream);
 
 /*
- * Counters of the last batched (KHOP_MODE_BATCHED64) launch on g: 64-lane
- * batches run, algorithmic HBM bytes (the method's compulsory traffic: lane
+ * Counters of the last batched launch on g (either lane width): batches run, algorithmic HBM bytes (the method's compulsory traffic: lane
  * words of the vertices and frontier items touched, edge indices read,
  * harvest sweeps), rounds and pull rounds.  Synchronises the device.  Any
  * pointer may be NULL.

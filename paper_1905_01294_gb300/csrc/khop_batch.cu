@@ -1,17 +1,17 @@
-// Bit-sliced 64-lane batched k-hop count.
+// Bit-sliced batched k-hop count, 64 * LW lanes (LW = 1 or 2 64-bit words).
 //
-// Up to 64 queries share one traversal: every vertex v carries three 64-bit
-// lane words -- V[v] (lanes that have visited v), F_in[v] / F_out[v] (lanes
+// Up to 64 * LW queries share one traversal: every vertex v carries three lane
+// words -- V[v] (lanes that have visited v), F_in[v] / F_out[v] (lanes
 // whose frontier holds v this round / next round) -- so the (OR, AND)
 // semiring of the single query becomes bitwise OR/AND on lane words:
 //     F_out[w] = (OR over edges u -> w of F_in[u]) AND NOT V[w] AND active
 // where `active` holds the lanes whose k has not been reached.  Lane j's count
 // is the number of set j-bits of V at the end, minus its seed.
 //
-// Queries are grouped on the device into batches of 64 by k (a counting sort
-// by min(k, 63)), so the lanes of a batch mostly finish together.  One
+// Queries are grouped on the device into batches of 64 * LW by k (a counting
+// sort by min(k, 63)), so the lanes of a batch mostly finish together.  One
 // cooperative persistent launch then runs every batch: rounds of push
-// (union-frontier queue, 64-bit atomicOr on V and F_out) or pull (lane-mask
+// (union-frontier queue, 64-bit atomicOr per lane word on V and F_out) or pull (lane-mask
 // OR over the in-edges of every vertex some active lane has not visited, with
 // an early exit once all those lanes are covered), chosen by a Beamer-style
 // switch on the union frontier; then a harvest sweep counts the lane bits of
@@ -39,7 +39,83 @@ constexpr int kStagePosShift = 40;
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
 constexpr uint32_t kEmpty = 0xffffffffu;
 
-template <typename E>
+// A lane word: LW 64-bit words, lane l in bit l % 64 of word l / 64.
+template <int LW>
+struct __align__(8 * LW) Lanes {
+    unsigned long long w[LW];
+};
+
+template <int LW>
+__device__ __forceinline__ Lanes<LW> lzero() {
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = 0ull;
+    return r;
+}
+template <int LW>
+__device__ __forceinline__ bool lany(const Lanes<LW> &x) {
+    unsigned long long o = 0ull;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) o |= x.w[j];
+    return o != 0ull;
+}
+template <int LW>
+__device__ __forceinline__ Lanes<LW> land(const Lanes<LW> &a, const Lanes<LW> &b) {
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = a.w[j] & b.w[j];
+    return r;
+}
+template <int LW>
+__device__ __forceinline__ Lanes<LW> landnot(const Lanes<LW> &a, const Lanes<LW> &b) {   // a & ~b
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = a.w[j] & ~b.w[j];
+    return r;
+}
+template <int LW>
+__device__ __forceinline__ void lor_into(Lanes<LW> &a, const Lanes<LW> &b) {
+#pragma unroll
+    for (int j = 0; j < LW; ++j) a.w[j] |= b.w[j];
+}
+template <int LW>
+__device__ __forceinline__ bool lcovers(const Lanes<LW> &acc, const Lanes<LW> &need) {   // need ⊆ acc
+    bool r = true;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r = r && ((acc.w[j] & need.w[j]) == need.w[j]);
+    return r;
+}
+template <int LW>
+__device__ __forceinline__ Lanes<LW> lbit(int l) {
+    Lanes<LW> r = lzero<LW>();
+    r.w[l >> 6] = 1ull << (l & 63);
+    return r;
+}
+// OR x into *p word by word (words of x that are zero are not touched);
+// returns the old value of the touched words (zero for the others).
+template <int LW>
+__device__ __forceinline__ Lanes<LW> latomic_or(Lanes<LW> *p, const Lanes<LW> &x) {
+    Lanes<LW> old;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) old.w[j] = x.w[j] ? atomicOr(&p->w[j], x.w[j]) : 0ull;
+    return old;
+}
+template <int LW>
+__device__ __forceinline__ Lanes<LW> lload_relaxed(const Lanes<LW> *p) {
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = ld_relaxed_u64(&p->w[j]);
+    return r;
+}
+template <int LW>
+__device__ __forceinline__ Lanes<LW> lshfl(const Lanes<LW> &x, int src) {
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = __shfl_sync(FULL, x.w[j], src);
+    return r;
+}
+
+template <typename E, int LW>
 struct BatchArgs {
     uint64_t n, nnz;
     uint32_t nw;
@@ -49,21 +125,21 @@ struct BatchArgs {
     const E *cp;
     const uint32_t *ri;
     const uint32_t *noin;
-    unsigned long long *V;
-    unsigned long long *F0, *F1, *F2;
+    Lanes<LW> *V;
+    Lanes<LW> *F0, *F1, *F2;
     uint32_t *Q0, *Q1;           // union-frontier queue: vertex ids
     E *Qpre0, *Qpre1;            // queue: out-edge prefix
     uint32_t *TF0, *TF1;         // first queue item of each push tile
     CtlBlock *ctl;
-    unsigned long long *part;    // per-CTA lane counts [2][grid][64], by batch parity
+    unsigned long long *part;    // per-CTA lane counts [2][grid][64 * LW], by batch parity
     const uint32_t *seeds;
     const uint32_t *ks;
     uint64_t *out;
-    const uint32_t *order;       // 64 query indices per batch (kEmpty = unused lane)
+    const uint32_t *order;       // 64 * LW query indices per batch (kEmpty = unused lane)
     const unsigned long long *nbatches;
     uint32_t *hv;                // deferred pull vertices
     E *hend;
-    unsigned long long *hneed, *hacc;
+    Lanes<LW> *hneed, *hacc;
     uint64_t hcap;
     uint32_t *ch_item;           // chunks of the deferred in-lists
     E *ch_start;
@@ -80,6 +156,7 @@ __device__ __forceinline__ T sel3(T x0, T x1, T x2, unsigned i) {
     return i == 0 ? x0 : (i == 1 ? x1 : x2);
 }
 
+template <int LW>
 struct Shared {
     unsigned long long cnt, mf, stage, limit, gbase, scan, unv;
     unsigned long long skipped;  // items not queued because the queue was past its cap
@@ -87,19 +164,19 @@ struct Shared {
     unsigned long long slot[8];
     int flag;
     // lane table of the current batch
-    uint32_t seed[64];
-    uint32_t k[64];
-    uint32_t qi[64];
-    unsigned long long deg_pre[65];   // round 1: exclusive prefix of the seeds' out-degrees
+    uint32_t seed[64 * LW];
+    uint32_t k[64 * LW];
+    uint32_t qi[64 * LW];
+    unsigned long long deg_pre[64 * LW + 1];   // round 1: exclusive prefix of the seeds' out-degrees
     uint32_t kmax;
 };
 
-template <typename E>
+template <typename E, int LW>
 struct Round {
     bool first, last;
-    unsigned long long act;      // lanes still running this round
-    const unsigned long long *Fin;
-    unsigned long long *Fout;
+    Lanes<LW> act;               // lanes still running this round
+    const Lanes<LW> *Fin;
+    Lanes<LW> *Fout;
     const uint32_t *Q_in;
     const E *Qpre_in;
     const uint32_t *TF_in;
@@ -110,8 +187,8 @@ struct Round {
     uint64_t cap, items_in, mf;
 };
 
-template <typename E>
-__device__ __forceinline__ void put_item(const BatchArgs<E> &a, const Round<E> &R, uint64_t pos,
+template <typename E, int LW>
+__device__ __forceinline__ void put_item(const BatchArgs<E, LW> &a, const Round<E, LW> &R, uint64_t pos,
                                          uint64_t pre, uint32_t w, E d) {
     if (pos >= R.cap) return;
     R.Q_out[pos] = w;
@@ -125,9 +202,9 @@ __device__ __forceinline__ void put_item(const BatchArgs<E> &a, const Round<E> &
 // frontier (with out-degree d > 0).  Union counts and out-edge sums go to the
 // CTA; unless this is the last round w joins the next queue through the
 // CTA's shared staging area (as in the single-query kernel).
-template <typename E>
-__device__ __forceinline__ void record(const BatchArgs<E> &a, const Round<E> &R, bool isnew,
-                                       uint32_t w, E d, Shared &sh, uint32_t *st_w, E *st_pre,
+template <typename E, int LW>
+__device__ __forceinline__ void record(const BatchArgs<E, LW> &a, const Round<E, LW> &R, bool isnew,
+                                       uint32_t w, E d, Shared<LW> &sh, uint32_t *st_w, E *st_pre,
                                        E *st_d) {
     const unsigned m = __ballot_sync(FULL, isnew);
     if (m == 0u) return;
@@ -177,8 +254,8 @@ __device__ __forceinline__ void record(const BatchArgs<E> &a, const Round<E> &R,
     }
 }
 
-template <typename E>
-__device__ __forceinline__ void flush_round(const BatchArgs<E> &a, const Round<E> &R, Shared &sh,
+template <typename E, int LW>
+__device__ __forceinline__ void flush_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, Shared<LW> &sh,
                                             uint32_t *st_w, E *st_pre, E *st_d,
                                             unsigned long long *slot_out) {
     __syncthreads();
@@ -214,14 +291,22 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E> &a, const Round<E
 // Visit w for the lanes in m: returns true if w entered the union frontier
 // (its first frontier lane this round) and has out-edges; d = out-degree.
 // The degree is read only for that first entry.
-template <typename E>
-__device__ __forceinline__ bool visit(const BatchArgs<E> &a, const Round<E> &R, uint32_t w,
-                                      unsigned long long m, E &d) {
-    const unsigned long long x = m & ~a.V[w];
-    if (!x) return false;
-    const unsigned long long nb = x & ~atomicOr(&a.V[w], x);
-    if (!nb || R.last) return false;
-    if (atomicOr(&R.Fout[w], nb) != 0ull) return false;
+template <typename E, int LW>
+__device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, LW> &R, uint32_t w,
+                                      const Lanes<LW> &m, E &d) {
+    const Lanes<LW> x = landnot(m, a.V[w]);
+    if (!lany(x)) return false;
+    const Lanes<LW> nb = landnot(x, latomic_or(&a.V[w], x));
+    if (!lany(nb) || R.last) return false;
+    // entry into the union frontier: a word of F_out[w] this call turned from
+    // zero to non-zero.  With one word that is exactly one caller per vertex;
+    // with LW words up to LW callers may queue w (extra work, same counts),
+    // and at least one always does.
+    const Lanes<LW> of = latomic_or(&R.Fout[w], nb);
+    bool entered = false;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) entered = entered || (nb.w[j] != 0ull && of.w[j] == 0ull);
+    if (!entered) return false;
     d = a.rp[w + 1] - a.rp[w];
     return d > 0;
 }
@@ -229,10 +314,10 @@ __device__ __forceinline__ bool visit(const BatchArgs<E> &a, const Round<E> &R, 
 // Push round.  Round 1 expands the lanes' seeds straight from the lane table
 // (item t = lane t, mask = its bit; a self-loop at the seed is skipped); later
 // rounds expand the union-frontier queue with each item's lanes F_in[u] & act.
-template <typename E>
-__device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E> &R, E *s_pre,
-                                           E *s_rs, unsigned long long *s_fm, uint32_t *s_u,
-                                           Shared &sh, uint32_t *st_w, E *st_pre, E *st_d) {
+template <typename E, int LW>
+__device__ __forceinline__ void push_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, E *s_pre,
+                                           E *s_rs, Lanes<LW> *s_fm, uint32_t *s_u,
+                                           Shared<LW> &sh, uint32_t *st_w, E *st_pre, E *st_d) {
     const uint32_t tl = a.tile_log2;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
@@ -241,13 +326,13 @@ __device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E>
         const uint64_t e1 = min(e0 + T, R.mf);
         uint32_t nitems;
         if (R.first) {
-            nitems = 64;
-            if (threadIdx.x < 64) {
+            nitems = 64 * LW;
+            if (threadIdx.x < 64 * LW) {
                 const int l = threadIdx.x;
-                const bool on = sh.qi[l] != kEmpty && ((R.act >> l) & 1ull);
+                const bool on = sh.qi[l] != kEmpty && ((R.act.w[l >> 6] >> (l & 63)) & 1ull);
                 s_pre[l] = (E)sh.deg_pre[l];
                 s_rs[l] = on ? a.rp[sh.seed[l]] : (E)0;
-                s_fm[l] = on ? (1ull << l) : 0ull;
+                s_fm[l] = on ? lbit<LW>(l) : lzero<LW>();
                 s_u[l] = on ? sh.seed[l] : kEmpty;
             }
         } else {
@@ -258,7 +343,7 @@ __device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E>
                 const uint32_t u = R.Q_in[i0 + t];
                 s_pre[t] = R.Qpre_in[i0 + t];
                 s_rs[t] = a.rp[u];
-                s_fm[t] = R.Fin[u] & R.act;
+                s_fm[t] = land(R.Fin[u], R.act);
                 s_u[t] = kEmpty;
             }
         }
@@ -266,12 +351,12 @@ __device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E>
         uint32_t hint = 0;
         for (uint64_t base = e0; base < e1; base += (uint64_t)kBlock * kPushUnroll) {
             uint32_t w[kPushUnroll];
-            unsigned long long m[kPushUnroll];
+            Lanes<LW> m[kPushUnroll];
 #pragma unroll
             for (int u = 0; u < kPushUnroll; ++u) {
                 const uint64_t e = base + (uint64_t)u * kBlock + threadIdx.x;
                 w[u] = 0;
-                m[u] = 0;
+                m[u] = lzero<LW>();
                 if (e < e1) {
                     uint32_t lo = hint, hi = nitems - 1;   // largest item with prefix <= e
                     while (lo < hi) {
@@ -280,16 +365,16 @@ __device__ __forceinline__ void push_round(const BatchArgs<E> &a, const Round<E>
                     }
                     hint = lo;
                     m[u] = s_fm[lo];
-                    if (m[u]) {
+                    if (lany(m[u])) {
                         w[u] = a.ci[(uint64_t)s_rs[lo] + (e - (uint64_t)s_pre[lo])];
-                        if (w[u] == s_u[lo]) m[u] = 0;   // round 1: a seed's self-loop
+                        if (w[u] == s_u[lo]) m[u] = lzero<LW>();   // round 1: a seed's self-loop
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kPushUnroll; ++u) {
                 E d = 0;
-                const bool isnew = m[u] && visit(a, R, w[u], m[u], d);
+                const bool isnew = lany(m[u]) && visit(a, R, w[u], m[u], d);
                 record(a, R, isnew, w[u], d, sh, st_w, st_pre, st_d);
             }
         }
@@ -303,6 +388,14 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
     return ((unsigned long long)hi << 32) | lo;
 }
 
+template <int LW>
+__device__ __forceinline__ Lanes<LW> warp_or(const Lanes<LW> &x) {
+    Lanes<LW> r;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) r.w[j] = warp_or64(x.w[j]);
+    return r;
+}
+
 // Pull round, sweep part.  Thread per vertex: need = act & ~V[v] (vertices
 // without in-edges are skipped); the vertex ORs the frontier lanes F_in[u]
 // of its in-neighbours until every needed lane is covered.  A lane first
@@ -310,8 +403,8 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
 // warp then takes the unresolved vertices one at a time, 32 * kPullILP
 // in-edges per step, OR-reducing across the warp.  In-lists with more than
 // kDeferEdges edges left are deferred to the chunked pass (pull_heavy).
-template <typename E>
-__device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E> &R, Shared &sh,
+template <typename E, int LW>
+__device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, Shared<LW> &sh,
                                            uint32_t *st_w, E *st_pre, E *st_d,
                                            unsigned long long *slot) {
     const int lane = threadIdx.x & 31;
@@ -321,45 +414,46 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
     for (uint64_t i = gwarp; i < a.nw; i += nwarps) {
         const uint64_t v = (i << 5) + (uint64_t)lane;
         const uint32_t ni = a.noin[i];
-        unsigned long long need = 0;
-        if (v < a.n && !((ni >> lane) & 1u)) need = R.act & ~a.V[v];
-        const unsigned nmask = __ballot_sync(FULL, need != 0ull);
+        Lanes<LW> need = lzero<LW>();
+        if (v < a.n && !((ni >> lane) & 1u)) need = landnot(R.act, a.V[v]);
+        const bool needs = lany(need);
+        const unsigned nmask = __ballot_sync(FULL, needs);
         if (nmask == 0u) {
-            if (v < a.n) R.Fout[v] = 0ull;
+            if (v < a.n) R.Fout[v] = lzero<LW>();
             continue;
         }
         unv += __popc(nmask);
         E b = 0, e = 0;
-        if (need) {
+        if (needs) {
             b = a.cp[v];
             e = a.cp[v + 1];
         }
-        unsigned long long acc = 0;
+        Lanes<LW> acc = lzero<LW>();
         E pos = b;
         for (int it = 0; it < kLaneEdges / kPullILP; ++it) {
-            const bool go = need && pos < e && (acc & need) != need;
+            const bool go = needs && pos < e && !lcovers(acc, need);
             if (!__any_sync(FULL, go)) break;
             uint32_t u[kPullILP];
 #pragma unroll
             for (int t = 0; t < kPullILP; ++t) u[t] = (go && pos + t < e) ? a.ri[pos + t] : kEmpty;
 #pragma unroll
             for (int t = 0; t < kPullILP; ++t)
-                if (u[t] != kEmpty) acc |= R.Fin[u[t]];
+                if (u[t] != kEmpty) lor_into(acc, R.Fin[u[t]]);
             if (go) {
                 const E took = min((E)kPullILP, e - pos);
                 pos += took;
                 scanned += (uint64_t)took;
             }
         }
-        const bool open = need && pos < e && (acc & need) != need;
+        const bool open = needs && pos < e && !lcovers(acc, need);
         const bool defer = open && (uint64_t)(e - pos) > (uint64_t)kDeferEdges;
         unsigned todo = __ballot_sync(FULL, open && !defer);
         while (todo) {
             const int L = __ffs(todo) - 1;
             const E vb = __shfl_sync(FULL, pos, L), ve = __shfl_sync(FULL, e, L);
-            const unsigned long long nd = __shfl_sync(FULL, need, L);
-            const unsigned long long a0 = __shfl_sync(FULL, acc, L);
-            unsigned long long wacc = 0;
+            const Lanes<LW> nd = lshfl(need, L);
+            const Lanes<LW> a0 = lshfl(acc, L);
+            Lanes<LW> wacc = lzero<LW>();
             for (E c = vb; c < ve; c += (E)(32 * kPullILP)) {
                 uint32_t u[kPullILP];
 #pragma unroll
@@ -369,11 +463,14 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
                 }
 #pragma unroll
                 for (int t = 0; t < kPullILP; ++t)
-                    if (u[t] != kEmpty) wacc |= R.Fin[u[t]];
+                    if (u[t] != kEmpty) lor_into(wacc, R.Fin[u[t]]);
                 if (lane == 0) scanned += (uint64_t)min((E)(32 * kPullILP), ve - c);
-                if (((warp_or64(wacc) | a0) & nd) == nd) break;
+                Lanes<LW> f = warp_or(wacc);
+                lor_into(f, a0);
+                if (lcovers(f, nd)) break;
             }
-            const unsigned long long fin = warp_or64(wacc) | a0;
+            Lanes<LW> fin = warp_or(wacc);
+            lor_into(fin, a0);
             if (lane == L) acc = fin;
             todo &= todo - 1u;
         }
@@ -396,14 +493,19 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
                 atomicOr(&a.ctl->err, (unsigned)KHOP_DEVERR_CAPACITY);
             }
         }
-        const unsigned long long nb = defer ? 0ull : (acc & need);
+        const Lanes<LW> nb = defer ? lzero<LW>() : land(acc, need);
+        const bool any_nb = lany(nb);
         if (v < a.n) {
             R.Fout[v] = nb;
-            if (nb) a.V[v] |= nb;
+            if (any_nb) {
+                Lanes<LW> vv = a.V[v];
+                lor_into(vv, nb);
+                a.V[v] = vv;
+            }
         }
         E d = 0;
-        if (nb && !R.last) d = a.symmetric ? e - b : a.rp[v + 1] - a.rp[v];
-        record(a, R, nb != 0ull && d > 0, (uint32_t)v, d, sh, st_w, st_pre, st_d);
+        if (any_nb && !R.last) d = a.symmetric ? e - b : a.rp[v + 1] - a.rp[v];
+        record(a, R, any_nb && d > 0, (uint32_t)v, d, sh, st_w, st_pre, st_d);
     }
     scanned = warp_sum(scanned);
     if (lane == 0) {
@@ -415,20 +517,20 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E> &a, const Round<E>
 // Pull round, chunked pass over the deferred long in-lists: one warp per
 // chunk of kChunk in-edges; each chunk's lane OR goes to its vertex's
 // accumulator, and a chunk is skipped once its vertex has every needed lane.
-template <typename E>
-__device__ __forceinline__ void pull_chunks(const BatchArgs<E> &a, const Round<E> &R,
-                                            uint64_t nchunks, Shared &sh) {
+template <typename E, int LW>
+__device__ __forceinline__ void pull_chunks(const BatchArgs<E, LW> &a, const Round<E, LW> &R,
+                                            uint64_t nchunks, Shared<LW> &sh) {
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
     uint64_t scanned = 0;
     for (uint64_t c = gwarp; c < nchunks; c += nwarps) {
         const uint32_t h = a.ch_item[c];
-        const unsigned long long nd = a.hneed[h];
-        if ((ld_relaxed_u64(&a.hacc[h]) & nd) == nd) continue;
+        const Lanes<LW> nd = a.hneed[h];
+        if (lcovers(lload_relaxed(&a.hacc[h]), nd)) continue;
         const E cb = a.ch_start[c];
         const E ce = min(cb + (E)kChunk, a.hend[h]);
-        unsigned long long wacc = 0;
+        Lanes<LW> wacc = lzero<LW>();
         int steps = 0;
         for (E x = cb; x < ce; x += (E)(32 * kPullILP)) {
             uint32_t u[kPullILP];
@@ -439,109 +541,124 @@ __device__ __forceinline__ void pull_chunks(const BatchArgs<E> &a, const Round<E
             }
 #pragma unroll
             for (int t = 0; t < kPullILP; ++t)
-                if (u[t] != kEmpty) wacc |= R.Fin[u[t]];
+                if (u[t] != kEmpty) lor_into(wacc, R.Fin[u[t]]);
             if (lane == 0) scanned += (uint64_t)min((E)(32 * kPullILP), ce - x);
-            if ((++steps & 7) == 0 &&
-                ((warp_or64(wacc) | ld_relaxed_u64(&a.hacc[h])) & nd) == nd)
-                break;
+            if ((++steps & 7) == 0) {
+                Lanes<LW> f = warp_or(wacc);
+                lor_into(f, lload_relaxed(&a.hacc[h]));
+                if (lcovers(f, nd)) break;
+            }
         }
-        const unsigned long long fin = warp_or64(wacc);
-        if (lane == 0 && (fin & nd)) atomicOr(&a.hacc[h], fin & nd);
+        const Lanes<LW> fin = land(warp_or(wacc), nd);
+        if (lane == 0 && lany(fin)) latomic_or(&a.hacc[h], fin);
     }
     scanned = warp_sum(scanned);
     if (lane == 0 && scanned) atomicAdd(&sh.scan, (unsigned long long)scanned);
 }
 
 // Pull round, last part: settle the deferred vertices (thread per item).
-template <typename E>
-__device__ __forceinline__ void pull_settle(const BatchArgs<E> &a, const Round<E> &R,
-                                            uint64_t nitems, Shared &sh, uint32_t *st_w,
+template <typename E, int LW>
+__device__ __forceinline__ void pull_settle(const BatchArgs<E, LW> &a, const Round<E, LW> &R,
+                                            uint64_t nitems, Shared<LW> &sh, uint32_t *st_w,
                                             E *st_pre, E *st_d) {
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
     const uint64_t iters = (nitems + gthreads - 1) / gthreads;   // uniform: record() is warp-wide
     for (uint64_t it = 0; it < iters; ++it) {
         const uint64_t h = gtid + it * gthreads;
-        unsigned long long nb = 0;
+        Lanes<LW> nb = lzero<LW>();
         uint32_t v = 0;
         E d = 0;
         if (h < nitems) {
             v = a.hv[h];
-            nb = a.hacc[h] & a.hneed[h];
-            a.hacc[h] = 0ull;
+            nb = land(a.hacc[h], a.hneed[h]);
+            a.hacc[h] = lzero<LW>();
             R.Fout[v] = nb;
-            if (nb) {
-                a.V[v] |= nb;
+            if (lany(nb)) {
+                Lanes<LW> vv = a.V[v];
+                lor_into(vv, nb);
+                a.V[v] = vv;
                 if (!R.last) d = a.rp[v + 1] - a.rp[v];
             }
         }
-        record(a, R, nb != 0ull && d > 0, v, d, sh, st_w, st_pre, st_d);
+        record(a, R, lany(nb) && d > 0, v, d, sh, st_w, st_pre, st_d);
     }
 }
 
 // Harvest: per-lane popcount of V over all vertices (bit-sliced counters per
-// thread, flushed with warp ballots), written to this CTA's row of `part`;
-// V is cleared on the way.
-__device__ __forceinline__ void harvest(unsigned long long *V, uint64_t n,
-                                        unsigned long long *part_row, unsigned *s_lane) {
+// thread and lane word, flushed with warp ballots), written to this CTA's row
+// of `part`; V is cleared on the way.
+template <int LW>
+__device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long long *part_row,
+                                        unsigned *s_lane) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 64) s_lane[threadIdx.x] = 0u;
+    if (threadIdx.x < 64 * LW) s_lane[threadIdx.x] = 0u;
     __syncthreads();
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
     const uint64_t iters = (n + gthreads - 1) / gthreads;   // uniform across the CTA
-    unsigned long long p[kPlanes];
+    unsigned long long p[kPlanes][LW];
 #pragma unroll
-    for (int i = 0; i < kPlanes; ++i) p[i] = 0ull;
+    for (int i = 0; i < kPlanes; ++i)
+#pragma unroll
+        for (int j = 0; j < LW; ++j) p[i][j] = 0ull;
     for (uint64_t it = 0; it < iters; ++it) {
         const uint64_t v = gtid + it * gthreads;
-        unsigned long long x = 0ull;
+        Lanes<LW> x = lzero<LW>();
         if (v < n) {
             x = V[v];
-            if (x) V[v] = 0ull;
+            if (lany(x)) V[v] = lzero<LW>();
         }
 #pragma unroll
-        for (int i = 0; i < kPlanes; ++i) {   // ripple-carry add of x into the planes
-            const unsigned long long c = p[i] & x;
-            p[i] ^= x;
-            x = c;
+        for (int j = 0; j < LW; ++j) {
+            unsigned long long y = x.w[j];
+#pragma unroll
+            for (int i = 0; i < kPlanes; ++i) {   // ripple-carry add of y into the planes
+                const unsigned long long c = p[i][j] & y;
+                p[i][j] ^= y;
+                y = c;
+            }
         }
         if ((it + 1) % 255 == 0 || it + 1 == iters) {
-            // lane l sums lane bits l and l + 32 over the warp
-            unsigned lo = 0, hi = 0;
 #pragma unroll
-            for (int i = 0; i < kPlanes; ++i) {
-                for (int j = 0; j < 32; ++j) {
-                    const unsigned cl = __popc(__ballot_sync(FULL, (p[i] >> j) & 1ull));
-                    const unsigned ch = __popc(__ballot_sync(FULL, (p[i] >> (j + 32)) & 1ull));
-                    if (lane == j) {
-                        lo += cl << i;
-                        hi += ch << i;
+            for (int j = 0; j < LW; ++j) {
+                // lane l sums lane bits l and l + 32 of word j over the warp
+                unsigned lo = 0, hi = 0;
+#pragma unroll
+                for (int i = 0; i < kPlanes; ++i) {
+                    for (int b = 0; b < 32; ++b) {
+                        const unsigned cl = __popc(__ballot_sync(FULL, (p[i][j] >> b) & 1ull));
+                        const unsigned ch = __popc(__ballot_sync(FULL, (p[i][j] >> (b + 32)) & 1ull));
+                        if (lane == b) {
+                            lo += cl << i;
+                            hi += ch << i;
+                        }
                     }
+                    p[i][j] = 0ull;
                 }
-                p[i] = 0ull;
+                if (lo) atomicAdd(&s_lane[64 * j + lane], lo);
+                if (hi) atomicAdd(&s_lane[64 * j + lane + 32], hi);
             }
-            if (lo) atomicAdd(&s_lane[lane], lo);
-            if (hi) atomicAdd(&s_lane[lane + 32], hi);
         }
     }
     __syncthreads();
-    if (threadIdx.x < 64) part_row[threadIdx.x] = s_lane[threadIdx.x];
+    if (threadIdx.x < 64 * LW) part_row[threadIdx.x] = s_lane[threadIdx.x];
 }
 
-template <typename E>
-__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) {
+template <typename E, int LW>
+__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW> a) {
+    constexpr int B = 64 * LW;   // lanes per batch
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const uint32_t T2 = (1u << a.tile_log2) + 2u;
-    unsigned long long *s_fm = (unsigned long long *)dyn_smem;       // [T2]
+    Lanes<LW> *s_fm = (Lanes<LW> *)dyn_smem;                         // [T2]
     E *s_pre = (E *)(s_fm + T2);                                     // [T2]
     E *s_rs = s_pre + T2;                                            // [T2]
     uint32_t *s_u = (uint32_t *)(s_rs + T2);                         // [T2]
     uint32_t *st_w = s_u + T2;                                       // [kStage]
     E *st_pre = (E *)(st_w + kStage);                                // [kStage]
     E *st_d = st_pre + kStage;                                       // [kStage]
-    __shared__ Shared sh;
-    __shared__ unsigned s_lane[64];
+    __shared__ Shared<LW> sh;
+    __shared__ unsigned s_lane[B];
 
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
@@ -562,10 +679,10 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     uint64_t rdone = dirty ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
     if (dirty)
         for (uint64_t v = gtid; v < a.n; v += gthreads) {
-            a.F0[v] = 0ull;
-            a.F1[v] = 0ull;
-            a.F2[v] = 0ull;
-            a.V[v] = 0ull;
+            a.F0[v] = lzero<LW>();
+            a.F1[v] = lzero<LW>();
+            a.F2[v] = lzero<LW>();
+            a.V[v] = lzero<LW>();
         }
     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
     if (gtid == 0) a.ctl->dirty = 1u;
@@ -573,9 +690,9 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     uint64_t bytes = 0, nrounds = 0, npull = 0;   // algorithmic HBM bytes, rounds run
     for (uint64_t b = 0; b < nb_total; ++b) {
         // lane table
-        if (threadIdx.x < 64) {
+        if (threadIdx.x < B) {
             const int l = threadIdx.x;
-            const uint32_t qi = a.order[b * 64 + l];
+            const uint32_t qi = a.order[b * B + l];
             sh.qi[l] = qi;
             sh.seed[l] = qi != kEmpty ? a.seeds[qi] : 0u;
             sh.k[l] = qi != kEmpty ? a.ks[qi] : 0u;
@@ -584,33 +701,33 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
         if (threadIdx.x == 0) {
             unsigned long long acc = 0;
             uint32_t kmax = 0;
-            for (int l = 0; l < 64; ++l) {
+            for (int l = 0; l < B; ++l) {
                 sh.deg_pre[l] = acc;
                 if (sh.qi[l] != kEmpty) {
                     acc += (unsigned long long)(a.rp[sh.seed[l] + 1] - a.rp[sh.seed[l]]);
                     kmax = max(kmax, sh.k[l]);
                 }
             }
-            sh.deg_pre[64] = acc;
+            sh.deg_pre[B] = acc;
             sh.kmax = kmax;
         }
         // seeds are visited by their own lanes
-        if (blockIdx.x == 0 && threadIdx.x < 64 && sh.qi[threadIdx.x] != kEmpty)
-            atomicOr(&a.V[sh.seed[threadIdx.x]], 1ull << threadIdx.x);
+        if (blockIdx.x == 0 && threadIdx.x < B && sh.qi[threadIdx.x] != kEmpty)
+            latomic_or(&a.V[sh.seed[threadIdx.x]], lbit<LW>(threadIdx.x));
         __syncthreads();
         const uint32_t kmax = sh.kmax;
-        uint64_t mf = sh.deg_pre[64], items = 64, nf = 64;
+        uint64_t mf = sh.deg_pre[B], items = B, nf = B;
         int prev = DIR_PUSH;
         for (uint32_t r = 1; r <= kmax && mf > 0; ++r) {
             ++rdone;
             const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
             const unsigned izero = (unsigned)((rdone + 1) % 3);
             const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
-            unsigned long long act = 0;
+            Lanes<LW> act = lzero<LW>();
             bool last = true;
-            for (int l = 0; l < 64; ++l)
+            for (int l = 0; l < B; ++l)
                 if (sh.qi[l] != kEmpty && sh.k[l] >= r) {
-                    act |= 1ull << l;
+                    act.w[l >> 6] |= 1ull << (l & 63);
                     if (sh.k[l] > r) last = false;
                 }
             int dir = DIR_PUSH;
@@ -618,8 +735,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
                 if (prev == DIR_PUSH) dir = ((double)mf * (double)a.alpha > (double)a.nnz) ? DIR_PULL : DIR_PUSH;
                 else dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap) ? DIR_PUSH : DIR_PULL;
             }
-            unsigned long long *Fz = sel3(a.F0, a.F1, a.F2, izero);
-            for (uint64_t v = gtid; v < a.n; v += gthreads) Fz[v] = 0ull;
+            Lanes<LW> *Fz = sel3(a.F0, a.F1, a.F2, izero);
+            for (uint64_t v = gtid; v < a.n; v += gthreads) Fz[v] = lzero<LW>();
             if (gtid == 0) {
                 slots[kSlotWords * izero + 0] = 0ull;
                 slots[kSlotWords * izero + 1] = 0ull;
@@ -629,7 +746,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
                 slots[kSlotWords * izero + 5] = 0ull;
                 slots[kSlotWords * izero + 6] = 0ull;
             }
-            Round<E> R;
+            Round<E, LW> R;
             R.first = r == 1;
             R.last = last;
             R.act = act;
@@ -646,32 +763,32 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             R.items_in = items;
             R.mf = mf;
             if (dir == DIR_PUSH)
-                push_round<E>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d);
+                push_round<E, LW>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d);
             else {
-                pull_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+                pull_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
                 // deferred long in-lists (counts read after a barrier: uniform)
                 if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout + 5,
                                   sh.slot + 5, 2, a.timeout_ns))
                     return;
                 const uint64_t nitems = min((uint64_t)sh.slot[5], a.hcap);
                 if (nitems) {
-                    pull_chunks<E>(a, R, min((uint64_t)sh.slot[6], a.ccap), sh);
+                    pull_chunks<E, LW>(a, R, min((uint64_t)sh.slot[6], a.ccap), sh);
                     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0,
                                       a.timeout_ns))
                         return;
-                    pull_settle<E>(a, R, nitems, sh, st_w, st_pre, st_d);
+                    pull_settle<E, LW>(a, R, nitems, sh, st_w, st_pre, st_d);
                 }
             }
-            flush_round<E>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+            flush_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot, 5,
                               a.timeout_ns))
                 return;
-            const uint64_t W = sizeof(E);
+            const uint64_t W = sizeof(E), LB = 8ull * LW;   // LB: bytes of a lane word
             const uint64_t items_out = last ? 0 : min((uint64_t)(sh.slot[0] >> a.ebits), R.cap);
             if (dir == DIR_PUSH)
-                bytes += items * (4 + 2 * W + 8) + 12ull * R.mf + items_out * (4 + W);
+                bytes += items * (4 + 2 * W + LB) + (4 + LB) * R.mf + items_out * (4 + W);
             else
-                bytes += 16ull * a.n + 4ull * a.nw + 2 * W * sh.slot[4] + 12ull * sh.slot[2] +
+                bytes += 2 * LB * a.n + 4ull * a.nw + 2 * W * sh.slot[4] + (4 + LB) * sh.slot[2] +
                          items_out * (4 + W);
             ++nrounds;
             if (dir == DIR_PULL) ++npull;
@@ -681,22 +798,22 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
             prev = dir;
         }
         // harvest the lane counts, clear V
-        bytes += 16ull * a.n;
-        unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * 64;
-        harvest(a.V, a.n, part + (uint64_t)blockIdx.x * 64, s_lane);
+        bytes += 16ull * LW * a.n;
+        unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * B;
+        harvest<LW>(a.V, a.n, part + (uint64_t)blockIdx.x * B, s_lane);
         if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
         if (blockIdx.x == 0) {
             // lane l is summed by the threads l, l + 64, ... over the CTAs
             __shared__ unsigned long long s_sum[kBlock];
-            const int l = threadIdx.x & 63;
+            const int l = threadIdx.x & (B - 1);
             unsigned long long acc = 0;
-            for (uint64_t c = threadIdx.x >> 6; c < gridDim.x; c += kBlock / 64)
-                acc += part[c * 64 + l];
+            for (uint64_t c = threadIdx.x / B; c < gridDim.x; c += kBlock / B)
+                acc += part[c * B + l];
             s_sum[threadIdx.x] = acc;
             __syncthreads();
-            if (threadIdx.x < 64) {
+            if (threadIdx.x < B) {
                 unsigned long long tot = 0;
-                for (int c = 0; c < kBlock / 64; ++c) tot += s_sum[c * 64 + l];
+                for (int c = 0; c < kBlock / B; ++c) tot += s_sum[c * B + l];
                 if (sh.qi[l] != kEmpty) a.out[sh.qi[l]] = tot - 1ull;   // minus the seed
             }
         }
@@ -712,8 +829,9 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E> a) 
     }
 }
 
-// Group the queries into batches of 64 by min(k, 63); answer k = 0 and
+// Group the queries into batches of 64 * LW by min(k, 63); answer k = 0 and
 // seeds >= n directly.  One CTA: histogram, padded exclusive scan, scatter.
+template <int LW>
 __global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, const uint32_t *ks,
                                                      uint64_t nq, uint64_t n, uint64_t *out,
                                                      uint32_t *order, uint64_t order_cap,
@@ -737,12 +855,12 @@ __global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, cons
         unsigned long long acc = 0;
         for (int b = 0; b < kBuckets; ++b) {
             base[b] = acc;
-            acc += (cnt[b] + 63) / 64 * 64;
+            acc += (cnt[b] + 64 * LW - 1) / (64 * LW) * (64 * LW);
         }
-        *nbatches = acc / 64;
+        *nbatches = acc / (64 * LW);
     }
     __syncthreads();
-    const unsigned long long total = *nbatches * 64;
+    const unsigned long long total = *nbatches * (64 * LW);
     for (uint64_t i = threadIdx.x; i < total && i < order_cap; i += blockDim.x) order[i] = kEmpty;
     __syncthreads();
     for (uint64_t i = threadIdx.x; i < nq; i += blockDim.x) {
@@ -755,10 +873,10 @@ __global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, cons
 }
 
 // Kernel arguments over a batch state.
-template <typename E>
-BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, const uint32_t *ks,
-                       uint64_t *out, const uint32_t *order, const unsigned long long *nbatches) {
-    BatchArgs<E> a;
+template <typename E, int LW>
+BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, const uint32_t *ks,
+                           uint64_t *out, const uint32_t *order, const unsigned long long *nbatches) {
+    BatchArgs<E, LW> a;
     a.n = g->n;
     a.nnz = g->nnz;
     a.nw = g->nw;
@@ -768,10 +886,10 @@ BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, con
     a.cp = (const E *)g->cp;
     a.ri = g->ri;
     a.noin = g->noin;
-    a.V = (unsigned long long *)bs.V;
-    a.F0 = (unsigned long long *)bs.F[0];
-    a.F1 = (unsigned long long *)bs.F[1];
-    a.F2 = (unsigned long long *)bs.F[2];
+    a.V = (Lanes<LW> *)bs.V;
+    a.F0 = (Lanes<LW> *)bs.F[0];
+    a.F1 = (Lanes<LW> *)bs.F[1];
+    a.F2 = (Lanes<LW> *)bs.F[2];
     a.Q0 = bs.Q[0];
     a.Q1 = bs.Q[1];
     a.Qpre0 = (E *)bs.Qpre[0];
@@ -787,8 +905,8 @@ BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, con
     a.nbatches = nbatches;
     a.hv = bs.hv;
     a.hend = (E *)bs.hend;
-    a.hneed = bs.hneed;
-    a.hacc = bs.hacc;
+    a.hneed = (Lanes<LW> *)bs.hneed;
+    a.hacc = (Lanes<LW> *)bs.hacc;
     a.hcap = bs.hcap;
     a.ch_item = bs.ch_item;
     a.ch_start = (E *)bs.ch_start;
@@ -797,6 +915,7 @@ BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, con
     a.beta = g->tune.batch_beta;
     uint32_t tl = 0;
     while ((1u << tl) < (uint32_t)g->tune.batch_push_tile) ++tl;
+    if (LW == 2 && tl > 12) tl = 12;   // 128 lanes: tiles of at most 4096 edges fit shared memory
     a.tile_log2 = tl;
     a.ebits = g->ebits;
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
@@ -807,11 +926,11 @@ BatchArgs<E> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, con
 
 // Cooperative launch of the batch kernel over `bs`; grid_ctas = 0 fills the
 // GPU, otherwise at most that many CTAs (so that several run side by side).
-template <typename E>
-int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E> &a, int grid_ctas, cudaStream_t st) {
+template <typename E, int LW>
+int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E, LW> &a, int grid_ctas, cudaStream_t st) {
     const size_t T2 = (size_t(1) << a.tile_log2) + 2;
-    const size_t smem = T2 * (8 + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
-    const void *fn = (const void *)batch_kernel<E>;
+    const size_t smem = T2 * (8 * LW + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
+    const void *fn = (const void *)batch_kernel<E, LW>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     int grid = 0;
@@ -824,12 +943,12 @@ int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E> &a, int grid_ctas,
     return cuda_status(e);
 }
 
-template <typename E>
+template <typename E, int LW>
 int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st) {
-    BatchState &bs = g->batch;
-    // order: nq plus up to 63 padding lanes per bucket
-    const uint64_t need = nq + 64ull * kBuckets;
+    BatchState &bs = LW == 2 ? g->batch2 : g->batch;
+    // order: nq plus up to 64 * LW - 1 padding lanes per bucket
+    const uint64_t need = nq + 64ull * LW * kBuckets;
     if (bs.order_cap < need) {
         cudaFree(bs.order);
         bs.order = nullptr;
@@ -840,13 +959,13 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     }
     cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
     if (e != cudaSuccess) return cuda_status(e);
-    group_kernel<<<1, 1024, 0, st>>>(seeds, ks, nq, g->n, out, bs.order, bs.order_cap,
-                                     (unsigned long long *)&bs.ctl->pad[0], &bs.ctl->err);
+    group_kernel<LW><<<1, 1024, 0, st>>>(seeds, ks, nq, g->n, out, bs.order, bs.order_cap,
+                                         (unsigned long long *)&bs.ctl->pad[0], &bs.ctl->err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
-    BatchArgs<E> a = make_args<E>(g, bs, seeds, ks, out, bs.order,
-                                  (const unsigned long long *)&bs.ctl->pad[0]);
-    return launch_kernel<E>(g, bs, a, 0, st);
+    BatchArgs<E, LW> a = make_args<E, LW>(g, bs, seeds, ks, out, bs.order,
+                                          (const unsigned long long *)&bs.ctl->pad[0]);
+    return launch_kernel<E, LW>(g, bs, a, 0, st);
 }
 
 template <typename E>
@@ -854,17 +973,21 @@ int slot_typed(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *o
                int grid_ctas, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
     if (e != cudaSuccess) return cuda_status(e);
-    BatchArgs<E> a = make_args<E>(g, bs, lanes, lanes + 64, out, lanes + 128,
-                                  (const unsigned long long *)(lanes + 192));
-    return launch_kernel<E>(g, bs, a, grid_ctas, st);
+    BatchArgs<E, 1> a = make_args<E, 1>(g, bs, lanes, lanes + 64, out, lanes + 128,
+                                        (const unsigned long long *)(lanes + 192));
+    return launch_kernel<E, 1>(g, bs, a, grid_ctas, st);
 }
 
 }  // namespace
 
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
-                 uint64_t *out, cudaStream_t st) {
-    if (g->ewidth == 4) return launch_typed<uint32_t>(g, seeds, ks, nq, out, st);
-    return launch_typed<unsigned long long>(g, seeds, ks, nq, out, st);
+                 uint64_t *out, cudaStream_t st, int lw) {
+    if (lw == 2) {
+        if (g->ewidth == 4) return launch_typed<uint32_t, 2>(g, seeds, ks, nq, out, st);
+        return launch_typed<unsigned long long, 2>(g, seeds, ks, nq, out, st);
+    }
+    if (g->ewidth == 4) return launch_typed<uint32_t, 1>(g, seeds, ks, nq, out, st);
+    return launch_typed<unsigned long long, 1>(g, seeds, ks, nq, out, st);
 }
 
 int batch_launch_slot(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,

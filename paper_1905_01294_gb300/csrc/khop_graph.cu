@@ -270,6 +270,7 @@ void free_graph(khop_graph *g) {
     cudaFree(g->noin);
     free_plain_state(g->plain);
     free_batch_state(g->batch);
+    free_batch_state(g->batch2);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
 }
@@ -370,31 +371,32 @@ int alloc_plain_state(khop_graph *g, PlainState &p) {
 
 // Allocate a bit-sliced batch state for graph g (no device sync needed by
 // the caller afterwards).  *bytes receives its size.
-int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes) {
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw) {
     const uint64_t n = g->n;
     const uint64_t before = g->device_bytes;
     b = BatchState{};
+    b.lw = lw;
     b.part_rows = (uint64_t)g->num_sms * 4;
     // a deferred in-list has more than 4096 edges left, so at most nnz / 4096
     // vertices defer per round, in at most 2 nnz / 4096 + 1 chunks of 4096
     b.hcap = std::min<uint64_t>(n, g->nnz / 4096 + 1);
     b.ccap = 2 * (g->nnz / 4096) + 2;
-    cudaError_t e = dalloc(g, &b.V, n);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n);
+    cudaError_t e = dalloc(g, &b.V, n * lw);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n * lw);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.Q[i], n);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &b.Qpre[i], n * g->ewidth);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &b.ctl, 1);
-    if (e == cudaSuccess) e = dalloc(g, &b.part, 2 * b.part_rows * 64);
+    if (e == cudaSuccess) e = dalloc(g, &b.part, 2 * b.part_rows * 64 * lw);
     if (e == cudaSuccess) e = dalloc(g, &b.hv, b.hcap);
     if (e == cudaSuccess) e = dalloc_raw(g, &b.hend, b.hcap * g->ewidth);
-    if (e == cudaSuccess) e = dalloc(g, &b.hneed, b.hcap);
-    if (e == cudaSuccess) e = dalloc(g, &b.hacc, b.hcap);
+    if (e == cudaSuccess) e = dalloc(g, &b.hneed, b.hcap * lw);
+    if (e == cudaSuccess) e = dalloc(g, &b.hacc, b.hcap * lw);
     if (e == cudaSuccess) e = dalloc(g, &b.ch_item, b.ccap);
     if (e == cudaSuccess) e = dalloc_raw(g, &b.ch_start, b.ccap * g->ewidth);
-    if (e == cudaSuccess) e = cudaMemset(b.hacc, 0, b.hcap * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(b.V, 0, n * sizeof(uint64_t));
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemset(b.hacc, 0, b.hcap * lw * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b.V, 0, n * lw * sizeof(uint64_t));
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * lw * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(CtlBlock));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -419,9 +421,10 @@ uint64_t plain_state_bytes(const khop_graph *g) {
     return 5ull * g->nw * 4 + 4 * g->n * (uint64_t)g->ewidth + 2 * g->tf_cap * 4 + sizeof(CtlBlock);
 }
 
-int ensure_batch_state(khop_graph *g) {
-    if (g->batch.V) return KHOP_OK;
-    return alloc_batch_state(g, g->batch, nullptr);
+int ensure_batch_state(khop_graph *g, int lw) {
+    BatchState &b = lw == 2 ? g->batch2 : g->batch;
+    if (b.V) return KHOP_OK;
+    return alloc_batch_state(g, b, nullptr, lw);
 }
 
 }  // namespace khop
@@ -701,8 +704,14 @@ int khop_get_error(khop_graph *g, uint32_t *bits) {
     e = cudaMemcpy(&a, &g->plain.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && g->batch.ctl)
         e = cudaMemcpy(&b, &g->batch.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && g->batch2.ctl) {
+        unsigned b2 = 0;
+        e = cudaMemcpy(&b2, &g->batch2.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        b |= b2;
+    }
     if (e == cudaSuccess) e = cudaMemset(&g->plain.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess && g->batch.ctl) e = cudaMemset(&g->batch.ctl->err, 0, sizeof(unsigned));
+    if (e == cudaSuccess && g->batch2.ctl) e = cudaMemset(&g->batch2.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     *bits = a | b;
     return cuda_status(e);

@@ -209,7 +209,8 @@ struct PlainState {
     uint64_t bytes = 0;
 };
 
-// Bit-sliced (64-lane) batch state of a graph.
+// Bit-sliced batch state of a graph: 64 * lw lanes per vertex word (lw 64-bit
+// words per vertex in V, F, and the deferred-in-list lane masks).
 struct BatchState {
     uint64_t *V = nullptr;                        // visited lanes per vertex [n]
     uint64_t *F[3] = {nullptr, nullptr, nullptr}; // frontier lanes per vertex [n], rotating
@@ -230,6 +231,7 @@ struct BatchState {
     void *ch_start = nullptr;                     // E
     uint64_t ccap = 0;
     size_t bytes = 0;
+    int lw = 1;
 };
 
 }  // namespace khop
@@ -253,7 +255,9 @@ struct khop_graph {
     uint64_t tf_cap = 0;                    // push-tile map entries
     khop::PlainState plain;                 // plain single-query traversal state
 
-    khop::BatchState batch;
+    khop::BatchState batch;                 // 64 lanes
+    khop::BatchState batch2;                // 128 lanes (allocated on first use)
+    int last_lw = 1;                        // lane width of the last batched call
 
     khop_tuning tune{};
     uint64_t timeout_ns = 2000000000ull;
@@ -271,8 +275,8 @@ namespace khop {
 int cuda_status(cudaError_t e);
 int order_after_previous(khop_graph *g, cudaStream_t s);   // call under g->mu
 int mark_done(khop_graph *g, cudaStream_t s);              // call under g->mu
-int ensure_batch_state(khop_graph *g);                     // call under g->mu
-int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes);  // a standalone state
+int ensure_batch_state(khop_graph *g, int lw = 1);         // call under g->mu
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw = 1);  // a standalone state
 int alloc_plain_state(khop_graph *g, PlainState &p);
 void free_plain_state(PlainState &p);
 void free_batch_state(BatchState &b);
@@ -293,9 +297,9 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                        uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st);
 
-// batched path (khop_batch.cu)
+// batched path (khop_batch.cu); lw = 1 (64 lanes) or 2 (128 lanes per traversal)
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
-                 uint64_t *out, cudaStream_t st);
+                 uint64_t *out, cudaStream_t st, int lw = 1);
 // One batch of up to 64 lanes on a standalone state.  `lanes` (device,
 // 8-byte aligned) holds seeds[64], ks[64], the lane order[64] (query index or
 // 0xffffffff) and then the 64-bit batch count (1).

@@ -25,66 +25,74 @@ def _device():
     kh.lib()
 
 
-def batched(G, seeds, ks):
+LANES = [kh.MODE_BATCHED64, kh.MODE_BATCHED128]   # 64 or 128 queries per traversal
+
+
+def batched(G, seeds, ks, mode=kh.MODE_BATCHED64):
     out = G.count_mixed(np.asarray(seeds, np.uint32), np.asarray(ks, np.uint32),
-                        mode=kh.MODE_BATCHED64)
+                        mode=mode)
     torch.cuda.synchronize()
     return kh.as_u64(out)
 
 
-def check(g, seeds, ks, wide=False, **tune):
+def check(g, seeds, ks, wide=False, mode=kh.MODE_BATCHED64, **tune):
     G = kh.Graph.from_csr(g, wide=wide)
     if tune:
         G.set_tuning(**tune)
     seeds = np.asarray(seeds, np.uint32)
     ks = np.broadcast_to(np.asarray(ks, np.uint32), seeds.shape).copy()
     want, _ = oracle.khop_counts(g, seeds, np.minimum(ks, g.n + 1))
-    got = batched(G, seeds, ks)
+    got = batched(G, seeds, ks, mode)
     np.testing.assert_array_equal(got, want)
     # lane/batch invariance: a permuted query order gives the same per-query counts
     perm = np.random.default_rng(len(seeds)).permutation(len(seeds))
-    got_p = batched(G, seeds[perm], ks[perm])
+    got_p = batched(G, seeds[perm], ks[perm], mode)
     np.testing.assert_array_equal(got_p, want[perm])
     bits = G.error_bits()
     G.close()
     return bits
 
 
-def test_rmat_scale10_mixed_k():
+@pytest.mark.parametrize("mode", LANES)
+def test_rmat_scale10_mixed_k(mode):
     g = gen.rmat(10, 16, seed=1)
     seeds = gen.seeds(g, 64, seed=2)
     ks = np.tile(np.array([1, 2, 3, 6], np.uint32), 16)
-    assert check(g, seeds, ks) == 0
+    assert check(g, seeds, ks, mode=mode) == 0
 
 
+@pytest.mark.parametrize("mode", LANES)
 @pytest.mark.parametrize("k", [1, 2, 3, 6])
-def test_rmat_scale10_every_vertex(k):
+def test_rmat_scale10_every_vertex(k, mode):
     g = gen.rmat(10, 16, seed=1)
-    assert check(g, np.arange(g.n, dtype=np.uint32), k) == 0
+    assert check(g, np.arange(g.n, dtype=np.uint32), k, mode=mode) == 0
 
 
-def test_symmetric_scale12_many_batches_wide():
+@pytest.mark.parametrize("mode", LANES)
+def test_symmetric_scale12_many_batches_wide(mode):
     g = gen.rmat(12, 16, seed=3, symmetrize=True)
     seeds = gen.seeds(g, 700, seed=4)
     ks = gen.mixed_ks(700, seed=5)
-    assert check(g, seeds, ks, wide=True) == 0
+    assert check(g, seeds, ks, wide=True, mode=mode) == 0
 
 
+@pytest.mark.parametrize("mode", LANES)
 @pytest.mark.parametrize("alpha,beta,tile", [(1e-6, 1e6, 256), (1e6, 1e-6, 8192), (14, 24, 1024)])
-def test_direction_extremes(alpha, beta, tile):
+def test_direction_extremes(alpha, beta, tile, mode):
     """alpha tiny: pull from round 2 on; alpha huge: push only."""
     g = gen.rmat(11, 16, seed=6)
     seeds = gen.seeds(g, 200, seed=7)
     ks = gen.mixed_ks(200, choices=(1, 2, 3, 4, 6), seed=8)
-    assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=beta, batch_push_tile=tile) == 0
+    assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=beta, batch_push_tile=tile, mode=mode) == 0
 
 
-def test_edge_cases_k0_bad_seed_duplicates_and_sinks():
+@pytest.mark.parametrize("mode", LANES)
+def test_edge_cases_k0_bad_seed_duplicates_and_sinks(mode):
     g = gen.csr_raw(40, [0, 0, 1, 2, 3, 3, 5, 5, 7], [1, 1, 2, 3, 0, 3, 5, 6, 7])
     seeds = np.array([0, 0, 0, 3, 39, 5, 7, 40, 1000, 2, 6, 1], np.uint32)
     ks = np.array([1, 2, 0, 6, 3, 2, 4, 2, 1, 2**31, 3, 5], np.uint32)
     G = kh.Graph.from_csr(g)
-    got = batched(G, seeds, ks)
+    got = batched(G, seeds, ks, mode)
     ok = seeds < g.n
     want, _ = oracle.khop_counts(g, seeds[ok], np.minimum(ks[ok], 100))
     np.testing.assert_array_equal(got[ok], want)
@@ -102,7 +110,8 @@ def test_small_named_graphs(n):
         assert check(g, seeds, ks) == 0
 
 
-def test_random_multigraphs():
+@pytest.mark.parametrize("mode", LANES)
+def test_random_multigraphs(mode):
     rng = np.random.default_rng(77)
     for _ in range(8):
         n = int(rng.integers(1, 400))
@@ -111,10 +120,11 @@ def test_random_multigraphs():
         nq = int(rng.integers(1, 200))
         seeds = rng.integers(0, n, nq).astype(np.uint32)
         ks = rng.choice([0, 1, 2, 3, 6, 9], nq).astype(np.uint32)
-        assert check(g, seeds, ks) == 0
+        assert check(g, seeds, ks, mode=mode) == 0
 
 
-def test_batched_equals_plain_on_scale21_mixed_workload():
+@pytest.mark.parametrize("mode", LANES)
+def test_batched_equals_plain_on_scale21_mixed_workload(mode):
     """4096 seeds with k uniform over {1,2,3,6} on the scale-21 symmetrized
     Kronecker graph: every batched count equals the plain path's count, and a
     sample of 256 equals the oracle's."""
@@ -122,7 +132,7 @@ def test_batched_equals_plain_on_scale21_mixed_workload():
     G = kh.Graph.from_csr(g)
     seeds = gen.seeds(g, 4096, seed=2)
     ks = gen.mixed_ks(4096, seed=2)
-    got = batched(G, seeds, ks)
+    got = batched(G, seeds, ks, mode)
     plain = G.count_mixed(seeds, ks, mode=kh.MODE_PLAIN)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(got, kh.as_u64(plain))
@@ -133,7 +143,8 @@ def test_batched_equals_plain_on_scale21_mixed_workload():
     G.close()
 
 
-def test_long_in_lists_deferred_to_chunks():
+@pytest.mark.parametrize("mode", LANES)
+def test_long_in_lists_deferred_to_chunks(mode):
     """A hub with 10,000 in-edges that the lanes seeded in a separate cycle
     never reach: with pull from round 2 on, every pull round scans the hub's
     whole in-list for those lanes (the chunked path), and counts still match."""
@@ -150,7 +161,7 @@ def test_long_in_lists_deferred_to_chunks():
                             np.arange(L + 2, L + 40, dtype=np.uint32)])
     ks = np.tile(np.array([1, 2, 3, 6, 9], np.uint32), len(seeds))[:len(seeds)]
     for alpha in (1e-6, 14.0):
-        assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=1e-6) == 0
+        assert check(g, seeds, ks, batch_alpha=alpha, batch_beta=1e-6, mode=mode) == 0
 
 
 def test_captured_cuda_graph_replays_batched_and_plain():
@@ -163,7 +174,7 @@ def test_captured_cuda_graph_replays_batched_and_plain():
     s = torch.from_numpy(seeds.view(np.int32)).cuda()
     k = torch.from_numpy(ks.view(np.int32)).cuda()
     want, _ = oracle.khop_counts(g, seeds, ks)
-    for mode in (kh.MODE_BATCHED64, kh.MODE_PLAIN):
+    for mode in (kh.MODE_BATCHED64, kh.MODE_BATCHED128, kh.MODE_PLAIN):
         out = torch.zeros(300, dtype=torch.int64, device="cuda")
         side = torch.cuda.Stream()
         with torch.cuda.stream(side):
