@@ -33,6 +33,12 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -110,7 +116,8 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // with barrier_sense(): the bit cannot flip before every CTA, this one
 // included, has arrived).  After a CTA-wide __syncthreads, thread 0 publishes
 // the CTA's writes with a gpu-scope release reduction (no reply to wait for)
-// and polls the word with acquire loads until the top bit flips.  The wait is
+// and polls the word with relaxed loads until the top bit flips, then fences
+// (acquire) before the rest of the CTA reads what the other CTAs wrote.  The wait is
 // bounded by `timeout_ns` of %globaltimer and by an iteration cap; on expiry
 // (or if another CTA already flagged a timeout) it sets KHOP_DEVERR_TIMEOUT in
 // *err and returns false, and the caller leaves the kernel.
@@ -146,7 +153,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, in
         sense ^= 0x80000000u;
         const uint64_t t0 = globaltimer_ns();
         uint64_t spins = 0;
-        while ((ld_acquire_u32(&bw->count) & 0x80000000u) != sense) {
+        while ((ld_relaxed_u32(&bw->count) & 0x80000000u) != sense) {
             ++spins;
             if ((spins & 255u) == 0u) {
                 if (ld_volatile_u32(err) & KHOP_DEVERR_TIMEOUT) { ok = 0; break; }
@@ -157,7 +164,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, in
                 }
             }
         }
-        fence_acq_rel_gpu();
+        fence_acq_rel_gpu();   // acquire: the flip was read relaxed
         for (int i = 0; i < post_n; ++i) post_dst[i] = ld_relaxed_u64(post_src + i);
         *s_flag = ok;
     } else if (threadIdx.x >= 32) {
