@@ -103,3 +103,23 @@ def test_rejects_bad_seed():
     with pytest.raises(kh.KhopError):
         G.neighbourhood(g.n, 2)
     G.close()
+
+
+def test_tiny_and_edgeless_graphs():
+    for g in (gen.empty_graph(1), gen.empty_graph(33), gen.csr_raw(2, [0, 0], [0, 1]),
+              gen.path_graph(2)):
+        G = kh.Graph.from_csr(g)
+        for s in range(g.n):
+            for k in (0, 1, 3):
+                want = want_set(g, s, k)
+                bits, cnt = G.neighbourhood(s, k)
+                ids, size = G.neighbourhood_list(s, k)
+                lv, par = G.levels(s, k)
+                torch.cuda.synchronize()
+                np.testing.assert_array_equal(bits_to_ids(bits, g.n), want)
+                np.testing.assert_array_equal(ids.cpu().numpy().view(np.uint32), want)
+                assert int(size.item()) == want.size and int(cnt.item()) == want.size - 1
+                np.testing.assert_array_equal(lv.cpu().numpy(), oracle.khop_dist(g, s, k))
+                np.testing.assert_array_equal(par.cpu().numpy().view(np.uint32),
+                                              oracle.bfs_parents(g, s, k))
+        G.close()
