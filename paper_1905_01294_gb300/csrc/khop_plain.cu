@@ -32,7 +32,7 @@ constexpr uint32_t kFuseDeg = 2048;          // seeds with at most this many out
                                              // first two rounds fused into one grid round
 constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
                                              // vertices are visited) read V before test-and-set
-constexpr int kPullWords = 4;    // bitmap words a warp works on at once in a pull round
+constexpr int kPullWords = 2;    // bitmap words a warp works on at once in a pull round
 constexpr int kFlatILP = 4;      // in-edges per lane per step of the flattened pull scan
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
 constexpr int kStagePosShift = 40;                       // staged count above, edges below
