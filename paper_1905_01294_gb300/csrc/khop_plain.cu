@@ -23,7 +23,7 @@ namespace {
 
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 
-constexpr int kPushUnroll = 4;   // edges in flight per thread in a push tile
+constexpr int kPushUnroll = 2;   // edges in flight per thread in a push tile
 constexpr uint64_t kPrefetchEdges = 2048;    // next-query seed edges warmed into L2
 constexpr uint32_t kSoloEdges = 2048;        // 1-hop queries with at most this many seed
                                              // out-edges run on one CTA
