@@ -96,27 +96,34 @@ __global__ void seed_level_kernel(int32_t *levels, uint32_t seed) { levels[seed]
 
 // BFS parents over the (MIN, SECOND) semiring: parent(v) = the smallest
 // in-neighbour u of v with level(u) = level(v) - 1 (v reached, v != s);
-// parent(s) = s; unreached vertices get UINT32_MAX.  One warp per vertex
-// over its in-list.
+// parent(s) = s; unreached vertices get UINT32_MAX.  A warp takes 32
+// consecutive vertices (one coalesced read of their levels), then scans the
+// in-lists of the reached ones together, one vertex at a time.
 template <typename E>
 __global__ void parents_kernel(const E *cp, const uint32_t *ri, const int32_t *levels, uint64_t n,
                                uint32_t *parents) {
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    for (uint64_t v = warp; v < n; v += nwarps) {
-        const int32_t lv = levels[v];
-        uint32_t best = 0xffffffffu;
-        if (lv > 0) {
-            for (E x = cp[v] + lane; x < cp[v + 1]; x += 32) {
-                const uint32_t u = ri[x];
-                if (levels[u] == lv - 1) best = min(best, u);
+    for (uint64_t base = warp << 5; base < n; base += nwarps << 5) {
+        const uint64_t v = base + (uint64_t)lane;
+        const int32_t lv = v < n ? levels[v] : -1;
+        uint32_t mine = lv == 0 ? (uint32_t)v : 0xffffffffu;
+        unsigned todo = __ballot_sync(FULL, lv > 0);
+        while (todo) {
+            const int L = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const uint64_t x = base + (uint64_t)L;
+            const int32_t want = __shfl_sync(FULL, lv, L) - 1;
+            uint32_t best = 0xffffffffu;
+            for (E i = cp[x] + lane; i < cp[x + 1]; i += 32) {
+                const uint32_t u = ri[i];
+                if (levels[u] == want) best = min(best, u);
             }
             for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL, best, o));
-        } else if (lv == 0) {
-            best = (uint32_t)v;
+            if (lane == L) mine = best;
         }
-        if (lane == 0) parents[v] = best;
+        if (v < n) parents[v] = mine;
     }
 }
 
