@@ -33,7 +33,7 @@ constexpr int kPullILP = 4;          // in-edge loads in flight per lane in a pu
 constexpr int kLaneEdges = 8;        // in-edges a lane scans alone before the warp helps
 constexpr int kDeferEdges = 4096;    // longer in-lists go to the chunked pass
 constexpr int kChunk = 4096;         // in-edges per chunk of the chunked pass
-constexpr int kPlanes = 8;           // bit-sliced counter planes (up to 255 additions)
+constexpr int kPlanes = 4;           // bit-sliced counter planes (up to 15 additions)
 constexpr int kStage = 2048;
 constexpr int kStagePosShift = 40;
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
@@ -619,7 +619,7 @@ __device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long 
                 y = c;
             }
         }
-        if ((it + 1) % 255 == 0 || it + 1 == iters) {
+        if ((it + 1) % ((1u << kPlanes) - 1u) == 0 || it + 1 == iters) {
 #pragma unroll
             for (int j = 0; j < LW; ++j) {
                 // lane l sums lane bits l and l + 32 of word j over the warp
