@@ -144,7 +144,7 @@ struct BatchArgs {
     uint32_t *ch_item;           // chunks of the deferred in-lists
     E *ch_start;
     uint64_t ccap;
-    float alpha, beta;
+    uint64_t alpha_fx, beta_fx;   // Beamer's alpha and beta in 1/65536 units
     uint32_t tile_log2, ebits;
     int stage;
     uint64_t pull_cap;
@@ -732,8 +732,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
                 }
             int dir = DIR_PUSH;
             if (r > 1) {
-                if (prev == DIR_PUSH) dir = ((double)mf * (double)a.alpha > (double)a.nnz) ? DIR_PULL : DIR_PUSH;
-                else dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap) ? DIR_PUSH : DIR_PULL;
+                if (prev == DIR_PUSH) dir = fx_gt(mf, a.alpha_fx, a.nnz) ? DIR_PULL : DIR_PUSH;
+                else dir = (fx_lt(nf, a.beta_fx, a.n) && items <= a.pull_cap) ? DIR_PUSH : DIR_PULL;
             }
             Lanes<LW> *Fz = sel3(a.F0, a.F1, a.F2, izero);
             for (uint64_t v = gtid; v < a.n; v += gthreads) Fz[v] = lzero<LW>();
@@ -911,8 +911,8 @@ BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds,
     a.ch_item = bs.ch_item;
     a.ch_start = (E *)bs.ch_start;
     a.ccap = bs.ccap;
-    a.alpha = g->tune.batch_alpha;
-    a.beta = g->tune.batch_beta;
+    a.alpha_fx = factor_fx16(g->tune.batch_alpha);
+    a.beta_fx = factor_fx16(g->tune.batch_beta);
     uint32_t tl = 0;
     while ((1u << tl) < (uint32_t)g->tune.batch_push_tile) ++tl;
     if (LW == 2 && tl > 12) tl = 12;   // 128 lanes: tiles of at most 4096 edges fit shared memory

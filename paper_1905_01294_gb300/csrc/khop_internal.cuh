@@ -126,31 +126,58 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // wait, so the rest of the CTA reads them from shared memory.
 // `overlap(t, nt)` runs on threads 32 .. blockDim.x - 1 (t = threadIdx.x - 32,
 // nt = blockDim.x - 32) while thread 0 waits: work that needs no ordering
-// against the barrier (prefetches).
+// against the barrier (prefetches).  `pre()` runs on every thread of the CTA
+// after its arrival and before its wait (a split barrier): work that reads
+// only data no CTA writes and writes only this CTA's shared memory.
 __device__ __forceinline__ unsigned barrier_sense(const BarrierWords *bw) {
     unsigned v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&bw->count) : "memory");
     return v & 0x80000000u;
 }
 
+// Beamer's direction tests (x * c > y, x * c < y for a tuning factor c) in
+// integer arithmetic: c is carried in 1/65536 units and both sides are
+// compared as 128-bit products.  The per-round decisions thus need no FP64,
+// whose rate on this part is a small fraction of the integer rate (a handful
+// of double operations by every warp of a CTA cost about a microsecond).
+inline uint64_t factor_fx16(float c) {
+    if (!(c > 0.0f)) return 0ull;
+    const double v = (double)c * 65536.0 + 0.5;
+    return v >= 4.0e18 ? 4000000000000000000ull : (uint64_t)v;
+}
+__device__ __forceinline__ bool fx_gt(uint64_t x, uint64_t c_fx, uint64_t y) {
+    return (unsigned __int128)x * c_fx > ((unsigned __int128)y << 16);
+}
+__device__ __forceinline__ bool fx_lt(uint64_t x, uint64_t c_fx, uint64_t y) {
+    return (unsigned __int128)x * c_fx < ((unsigned __int128)y << 16);
+}
+
 struct NoOverlap {
     __device__ void operator()(unsigned, unsigned) const {}
 };
 
-template <typename Overlap = NoOverlap>
+struct NoPre {
+    __device__ void operator()() const {}
+};
+
+template <typename Overlap = NoOverlap, typename Pre = NoPre>
 __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, int *s_flag,
                                              unsigned &sense,
                                              const unsigned long long *post_src = nullptr,
                                              unsigned long long *post_dst = nullptr,
                                              int post_n = 0, uint64_t timeout_ns = 2000000000ull,
-                                             const Overlap &overlap = Overlap()) {
+                                             const Overlap &overlap = Overlap(),
+                                             const Pre &pre = Pre()) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
         const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
         asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bw->count), "r"(add)
                      : "memory");
         sense ^= 0x80000000u;
+    }
+    pre();
+    if (threadIdx.x == 0) {
+        int ok = 1;
         const uint64_t t0 = globaltimer_ns();
         uint64_t spins = 0;
         while ((ld_relaxed_u32(&bw->count) & 0x80000000u) != sense) {

@@ -66,7 +66,7 @@ struct PlainArgs {
     int direction;
     int keep_v;              // every query on the grid path (the visited bitmap is wanted)
     int32_t *levels;         // or null: levels[w] = r when round r discovers w
-    float alpha, beta;
+    uint64_t alpha_fx, beta_fx;   // Beamer's alpha and beta in 1/65536 units
     uint32_t tile_log2;
     uint32_t ebits;
     int stage;               // stage queue items per CTA (needs nnz < 2^40)
@@ -878,6 +878,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
 
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
     unsigned par = 0;     // which visited bitmap the current query uses
+    bool pre_have = false;   // the current query's fused prelude already ran
+    uint32_t pre_m1 = 0;     //   (at the previous query's last barrier) and its m1
     while (q < a.nq) {
         if (!a.keep_v && solo_query(cur, all_pull)) {
             if (blockIdx.x == 0)
@@ -932,9 +934,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             else {
                 const uint64_t mu = a.nnz - (sum_mf + mf);   // out-edges of unvisited vertices
                 if (prev == DIR_PUSH)
-                    dir = ((double)mf * (double)a.alpha > (double)mu) ? DIR_PULL : DIR_PUSH;
+                    dir = fx_gt(mf, a.alpha_fx, mu) ? DIR_PULL : DIR_PUSH;
                 else
-                    dir = ((double)nf * (double)a.beta < (double)a.n && items <= a.pull_cap)
+                    dir = (fx_lt(nf, a.beta_fx, a.n) && items <= a.pull_cap)
                               ? DIR_PUSH : DIR_PULL;
             }
             // Zero what round r+1 writes (last read in round r-1).
@@ -955,10 +957,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             uint64_t mf2 = 0;
             bool fused = false;
             if (r == 1 && k >= 2 && !all_pull && a.stage && mf <= (uint64_t)kFuseDeg) {
-                m1 = fused_prelude<E, BLOCK>(a, s, cur.rs, (uint32_t)mf, s_nbr, s_npos, s_pre, s_rs, sh);
+                m1 = pre_have ? pre_m1
+                              : fused_prelude<E, BLOCK>(a, s, cur.rs, (uint32_t)mf, s_nbr, s_npos, s_pre, s_rs, sh);
+                pre_have = false;
                 mf2 = (uint64_t)s_pre[m1];
                 const uint64_t mu = a.nnz - (mf + mf2);
-                fused = a.direction == KHOP_DIR_PUSH || !((double)mf2 * (double)a.alpha > (double)mu);
+                fused = a.direction == KHOP_DIR_PUSH || !fx_gt(mf2, a.alpha_fx, mu);
                 if (fused && blockIdx.x == 0)   // q_1 visited (round 2 skips it)
                     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
                         const uint32_t x = s_nbr[i];
@@ -1016,9 +1020,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                 if (!pf) return;
                 for (uint64_t e = t; e < pf_d; e += nt) prefetch_l2(a.rp + a.ci[(uint64_t)pf_rs + e]);
             };
+            // After a query's last round, the next query's fused prelude (it
+            // reads only the graph and fills this CTA's shared tables) runs
+            // between this CTA's arrival and its wait.
+            const bool do_pre = R.last && qn < a.nq && nxt.k >= 2 && !all_pull && a.stage &&
+                                (uint64_t)(nxt.re - nxt.rs) <= (uint64_t)kFuseDeg;
+            const auto pre_next = [&]() {
+                if (!do_pre) return;
+                if (fused) {
+                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+                        s_nbr[i] = kHashEmpty;
+                        s_npos[i] = 0xffffffffu;
+                    }
+                    __syncthreads();
+                }
+                pre_m1 = fused_prelude<E, BLOCK>(a, nxt.s, nxt.rs, (uint32_t)(nxt.re - nxt.rs), s_nbr, s_npos,
+                                                 s_pre, s_rs, sh);
+            };
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot,
-                              (R.last && blockIdx.x != 0) ? 0 : 4, a.timeout_ns, prefetch_next))
+                              (R.last && blockIdx.x != 0) ? 0 : 4, a.timeout_ns, prefetch_next, pre_next))
                 return;
+            pre_have = do_pre;
             const unsigned long long qp = sh.slot[0];
             const uint64_t nnew = sh.slot[1];
             const uint64_t scn = sh.slot[2];
@@ -1026,10 +1048,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             const uint64_t items_out = R.last ? 0 : min((uint64_t)(qp >> a.ebits), R.cap);
             if (fused) {
                 // rounds 1 and 2: q_1 (m1 vertices) was listed by every CTA
-                for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
-                    s_nbr[i] = kHashEmpty;
-                    s_npos[i] = 0xffffffffu;
-                }
+                if (!do_pre)
+                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
+                        s_nbr[i] = kHashEmpty;
+                        s_npos[i] = 0xffffffffu;
+                    }
                 bytes += 4ull * mf + 2ull * W * (1ull + m1);
                 bytes += 4ull * mf2 + 2ull * W * (m1 + items_out);
                 te += mf2;
@@ -1154,8 +1177,8 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
     a.direction = g->tune.direction;
     a.keep_v = keep_visited || levels ? 1 : 0;
     a.levels = levels;
-    a.alpha = g->tune.alpha;
-    a.beta = g->tune.beta;
+    a.alpha_fx = factor_fx16(g->tune.alpha);
+    a.beta_fx = factor_fx16(g->tune.beta);
     uint32_t tl = 0;
     while ((1u << tl) < (uint32_t)g->tune.push_tile) ++tl;
     a.tile_log2 = tl;
@@ -1323,8 +1346,8 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     a.direction = has_csc ? KHOP_DIR_AUTO : KHOP_DIR_PUSH;
     a.keep_v = 0;
     a.levels = nullptr;
-    a.alpha = 14.0f;
-    a.beta = 24.0f;
+    a.alpha_fx = factor_fx16(14.0f);
+    a.beta_fx = factor_fx16(24.0f);
     a.tile_log2 = 11;   // 2048-edge push tiles
     uint32_t bl = 0;
     for (uint64_t x = n; x; x >>= 1) ++bl;
