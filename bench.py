@@ -333,6 +333,32 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
         raise SystemExit("128-lane counts differ from the 64-lane ones")
     lanes128 = {"value": nq * steps / (sum(ms128) * 1e-3), "unit": "queries/s",
                 "ms_per_step": float(np.mean(ms128)), "mode": "KHOP_MODE_BATCHED128 (direct calls)"}
+    # six-hop traversals alone: 1024 seeds (seed 4) at k = 6, 64 per lane word
+    n6 = min(1024, nq)
+    s6 = torch.from_numpy(gen.seeds(g, n6, seed=4).view(np.int32)).to(dev)
+    k6 = torch.full((n6,), 6, dtype=torch.int32, device=dev)
+    o6 = torch.empty(n6, dtype=torch.int64, device=dev)
+    six = {"queries": n6}
+    for mode, name in ((kh.MODE_BATCHED64, "lanes64"), (kh.MODE_BATCHED128, "lanes128")):
+        kh.khop_count_mixed(G.handle, s6.data_ptr(), k6.data_ptr(), n6, o6.data_ptr(), mode,
+                            stream.cuda_stream)
+        torch.cuda.synchronize()
+        ms6, b6 = 0.0, 0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kh.khop_count_mixed(G.handle, s6.data_ptr(), k6.data_ptr(), n6, o6.data_ptr(), mode,
+                                stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            ms6 += a.elapsed_time(b)
+            b6 += kh.khop_batch_stats(G.handle)["bytes"]
+        ach = b6 / (ms6 * 1e-3) / 1e9
+        six[name] = {"value": n6 * steps / (ms6 * 1e-3), "unit": "queries/s",
+                     "ms_per_call": ms6 / steps,
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak}}
     return {"workload": f"{gname}, {nq} seeds (seed 2), k uniform over {{1,2,3,6}}, "
                         "64 queries per uint64 lane word, persistent launch replayed from a "
                         "captured CUDA graph",
@@ -346,7 +372,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": captured_traffic("batch_kernel"),
                          "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"},
-            "lanes128": lanes128}
+            "lanes128": lanes128, "six_hop": six}
 
 
 K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
@@ -597,6 +623,7 @@ def main():
            for _ in range(args.steps)]
     lat, te_sum, bytes_sum = [], 0, 0
     lat_by_k = {k: [] for k, _ in PAPER_QUERIES}
+    bytes_by_k = {k: 0 for k, _ in PAPER_QUERIES}
     for i in range(args.steps):
         flush.fill_(i & 0xFF)                       # L2 flush between steps (not timed)
         evs[i][0].record(stream)
@@ -608,6 +635,7 @@ def main():
         lat.extend(dt.tolist())
         for k, _ in PAPER_QUERIES:
             lat_by_k[k].extend(dt[ks == k].tolist())
+            bytes_by_k[k] += int(rec["bytes"][ks == k].sum())
         te_sum += int(rec["te"].sum())
         bytes_sum += int(rec["bytes"].sum())
         if not np.array_equal(kh.as_u64(d_out), ref_counts):
@@ -652,6 +680,14 @@ def main():
                 "frac": achieved / peak, "traffic": captured_traffic("plain_kernel"),
                 "kernel": "plain_kernel (persistent push/pull traversal)",
                 "peak_kind": peak_kind}
+    # per k: the queries' algorithmic bytes over their device-timestamp latencies
+    roofline_by_k = {}
+    for k, _ in PAPER_QUERIES:
+        t_k = float(np.sum(lat_by_k[k])) * 1e-6
+        if t_k > 0:
+            a_k = bytes_by_k[k] / t_k / 1e9
+            roofline_by_k[str(k)] = {"achieved": a_k, "frac": a_k / peak,
+                                     "bytes_per_query": bytes_by_k[k] / max(1, len(lat_by_k[k]))}
 
     extras = {}
     if not args.no_extras:
@@ -688,6 +724,7 @@ def main():
         "latency_us_by_k": {str(k): percentiles(v) for k, v in lat_by_k.items()},
         "e2e": e2e,
         "roofline": roofline,
+        "roofline_by_k": roofline_by_k,
         "gpu_launches": args.steps,   # one persistent plain_kernel launch per step
         "clocks": clocks,
     }

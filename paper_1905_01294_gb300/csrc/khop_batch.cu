@@ -100,6 +100,14 @@ __device__ __forceinline__ Lanes<LW> latomic_or(Lanes<LW> *p, const Lanes<LW> &x
     for (int j = 0; j < LW; ++j) old.w[j] = x.w[j] ? atomicOr(&p->w[j], x.w[j]) : 0ull;
     return old;
 }
+// The same OR without the old value (a fire-and-forget reduction).
+template <int LW>
+__device__ __forceinline__ void lred_or(Lanes<LW> *p, const Lanes<LW> &x) {
+#pragma unroll
+    for (int j = 0; j < LW; ++j)
+        if (x.w[j])
+            asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(&p->w[j]), "l"(x.w[j]) : "memory");
+}
 template <int LW>
 __device__ __forceinline__ Lanes<LW> lload_relaxed(const Lanes<LW> *p) {
     Lanes<LW> r;
@@ -290,14 +298,20 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E, LW> &a, const Rou
 
 // Visit w for the lanes in m: returns true if w entered the union frontier
 // (its first frontier lane this round) and has out-edges; d = out-degree.
-// The degree is read only for that first entry.
+// The degree is read only for that first entry.  In a batch's last round
+// the lanes are ORed in without reading the old bits back (the harvest
+// counts V), so no thread waits on the atomic.
 template <typename E, int LW>
 __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, LW> &R, uint32_t w,
                                       const Lanes<LW> &m, E &d) {
     const Lanes<LW> x = landnot(m, a.V[w]);
     if (!lany(x)) return false;
+    if (R.last) {   // the harvest counts V: nothing needs the old bits
+        lred_or(&a.V[w], x);
+        return false;
+    }
     const Lanes<LW> nb = landnot(x, latomic_or(&a.V[w], x));
-    if (!lany(nb) || R.last) return false;
+    if (!lany(nb)) return false;
     // entry into the union frontier: a word of F_out[w] this call turned from
     // zero to non-zero.  With one word that is exactly one caller per vertex;
     // with LW words up to LW callers may queue w (extra work, same counts),
@@ -585,11 +599,17 @@ __device__ __forceinline__ void pull_settle(const BatchArgs<E, LW> &a, const Rou
     }
 }
 
-// Harvest: per-lane popcount of V over all vertices (bit-sliced counters per
-// thread and lane word, flushed with warp ballots), written to this CTA's row
-// of `part`; V is cleared on the way.
+// Harvest: per-lane popcount of V over all vertices, added into `row`
+// (64 * LW lane totals); V is cleared on the way.  Each thread keeps, per
+// lane word, kPlanes bit-sliced counters (plane i holds bit i of the 64 lane
+// counts), adding one V word per step with a ripple carry; every 15 steps the
+// warp sums its 32 threads' counters with a butterfly of bit-sliced adds
+// (five shuffle levels, one more plane per level: at most 15 * 32 < 2^9),
+// after which lane l reads the counts of bits l and l + 32 from the planes.
+constexpr int kSumPlanes = kPlanes + 5;
+
 template <int LW>
-__device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long long *part_row,
+__device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long long *row,
                                         unsigned *s_lane) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 64 * LW) s_lane[threadIdx.x] = 0u;
@@ -622,27 +642,38 @@ __device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long 
         if ((it + 1) % ((1u << kPlanes) - 1u) == 0 || it + 1 == iters) {
 #pragma unroll
             for (int j = 0; j < LW; ++j) {
-                // lane l sums lane bits l and l + 32 of word j over the warp
+                unsigned long long q[kSumPlanes];
+#pragma unroll
+                for (int i = 0; i < kSumPlanes; ++i) q[i] = i < kPlanes ? p[i][j] : 0ull;
+#pragma unroll
+                for (int lv = 0; lv < 5; ++lv) {   // q += q of lane ^ 2^lv
+                    unsigned long long c = 0ull;
+#pragma unroll
+                    for (int i = 0; i < kSumPlanes; ++i) {
+                        if (i > kPlanes + lv) break;   // planes above the current width are 0
+                        const unsigned long long o = __shfl_xor_sync(FULL, q[i], 1 << lv);
+                        const unsigned long long t = q[i] ^ o;
+                        const unsigned long long cn = (q[i] & o) | (c & t);
+                        q[i] = t ^ c;
+                        c = cn;
+                    }
+                }
                 unsigned lo = 0, hi = 0;
 #pragma unroll
-                for (int i = 0; i < kPlanes; ++i) {
-                    for (int b = 0; b < 32; ++b) {
-                        const unsigned cl = __popc(__ballot_sync(FULL, (p[i][j] >> b) & 1ull));
-                        const unsigned ch = __popc(__ballot_sync(FULL, (p[i][j] >> (b + 32)) & 1ull));
-                        if (lane == b) {
-                            lo += cl << i;
-                            hi += ch << i;
-                        }
-                    }
-                    p[i][j] = 0ull;
+                for (int i = 0; i < kSumPlanes; ++i) {
+                    lo |= (unsigned)((q[i] >> lane) & 1ull) << i;
+                    hi |= (unsigned)((q[i] >> (lane + 32)) & 1ull) << i;
                 }
+#pragma unroll
+                for (int i = 0; i < kPlanes; ++i) p[i][j] = 0ull;
                 if (lo) atomicAdd(&s_lane[64 * j + lane], lo);
                 if (hi) atomicAdd(&s_lane[64 * j + lane + 32], hi);
             }
         }
     }
     __syncthreads();
-    if (threadIdx.x < 64 * LW) part_row[threadIdx.x] = s_lane[threadIdx.x];
+    if (threadIdx.x < 64 * LW && s_lane[threadIdx.x])
+        atomicAdd(row + threadIdx.x, (unsigned long long)s_lane[threadIdx.x]);
 }
 
 template <typename E, int LW>
@@ -659,6 +690,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
     E *st_d = st_pre + kStage;                                       // [kStage]
     __shared__ Shared<LW> sh;
     __shared__ unsigned s_lane[B];
+    __shared__ unsigned long long s_deg[B];
+    __shared__ uint32_t s_kx[B];
 
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
@@ -677,6 +710,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
     unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
     const bool dirty = ld_volatile_u32(&a.ctl->dirty) != 0u;
     uint64_t rdone = dirty ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
+    if (gtid < 2ull * B) a.part[gtid] = 0ull;   // the two lane-total rows
     if (dirty)
         for (uint64_t v = gtid; v < a.n; v += gthreads) {
             a.F0[v] = lzero<LW>();
@@ -693,23 +727,36 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
         if (threadIdx.x < B) {
             const int l = threadIdx.x;
             const uint32_t qi = a.order[b * B + l];
+            const uint32_t sd = qi != kEmpty ? a.seeds[qi] : 0u;
+            const uint32_t kk = qi != kEmpty ? a.ks[qi] : 0u;
             sh.qi[l] = qi;
-            sh.seed[l] = qi != kEmpty ? a.seeds[qi] : 0u;
-            sh.k[l] = qi != kEmpty ? a.ks[qi] : 0u;
+            sh.seed[l] = sd;
+            sh.k[l] = kk;
+            s_deg[l] = qi != kEmpty ? (unsigned long long)(a.rp[sd + 1] - a.rp[sd]) : 0ull;
+            s_kx[l] = qi != kEmpty ? kk : 0u;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long acc = 0;
-            uint32_t kmax = 0;
-            for (int l = 0; l < B; ++l) {
-                sh.deg_pre[l] = acc;
-                if (sh.qi[l] != kEmpty) {
-                    acc += (unsigned long long)(a.rp[sh.seed[l] + 1] - a.rp[sh.seed[l]]);
-                    kmax = max(kmax, sh.k[l]);
-                }
+        if (threadIdx.x < 32) {   // exclusive prefix of the seeds' out-degrees, max k
+            constexpr int P = B / 32;
+            const int t = threadIdx.x;
+            unsigned long long d[P], sum = 0;
+            uint32_t km = 0;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                d[j] = s_deg[t * P + j];
+                sum += d[j];
+                km = max(km, s_kx[t * P + j]);
             }
-            sh.deg_pre[B] = acc;
-            sh.kmax = kmax;
+            const unsigned long long incl = warp_inclusive_sum(sum);
+            unsigned long long acc = incl - sum;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                sh.deg_pre[t * P + j] = acc;
+                acc += d[j];
+            }
+            if (t == 31) sh.deg_pre[B] = acc;
+            km = __reduce_max_sync(FULL, km);
+            if (t == 0) sh.kmax = km;
         }
         // seeds are visited by their own lanes
         if (blockIdx.x == 0 && threadIdx.x < B && sh.qi[threadIdx.x] != kEmpty)
@@ -797,25 +844,18 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
             mf = last ? 0 : sh.slot[3];
             prev = dir;
         }
-        // harvest the lane counts, clear V
+        // harvest the lane counts, clear V: every CTA adds its lane counts
+        // into the row of this batch's parity; CTA 0 reads the totals after
+        // the barrier and zeroes the row for batch b + 2.
         bytes += 16ull * LW * a.n;
-        unsigned long long *part = a.part + (b & 1) * (uint64_t)gridDim.x * B;
-        harvest<LW>(a.V, a.n, part + (uint64_t)blockIdx.x * B, s_lane);
+        unsigned long long *row = a.part + (b & 1) * (uint64_t)B;
+        harvest<LW>(a.V, a.n, row, s_lane);
         if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
-        if (blockIdx.x == 0) {
-            // lane l is summed by the threads l, l + 64, ... over the CTAs
-            __shared__ unsigned long long s_sum[kBlock];
-            const int l = threadIdx.x & (B - 1);
-            unsigned long long acc = 0;
-            for (uint64_t c = threadIdx.x / B; c < gridDim.x; c += kBlock / B)
-                acc += part[c * B + l];
-            s_sum[threadIdx.x] = acc;
-            __syncthreads();
-            if (threadIdx.x < B) {
-                unsigned long long tot = 0;
-                for (int c = 0; c < kBlock / B; ++c) tot += s_sum[c * B + l];
-                if (sh.qi[l] != kEmpty) a.out[sh.qi[l]] = tot - 1ull;   // minus the seed
-            }
+        if (blockIdx.x == 0 && threadIdx.x < B) {
+            const int l = threadIdx.x;
+            const unsigned long long tot = row[l];
+            row[l] = 0ull;
+            if (sh.qi[l] != kEmpty) a.out[sh.qi[l]] = tot - 1ull;   // minus the seed
         }
         __syncthreads();
     }
