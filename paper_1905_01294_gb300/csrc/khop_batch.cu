@@ -692,6 +692,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
     __shared__ unsigned s_lane[B];
     __shared__ unsigned long long s_deg[B];
     __shared__ uint32_t s_kx[B];
+    __shared__ unsigned s_act[B / 32], s_more[B / 32];
 
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
@@ -770,13 +771,27 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
             const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
             const unsigned izero = (unsigned)((rdone + 1) % 3);
             const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
-            Lanes<LW> act = lzero<LW>();
-            bool last = true;
-            for (int l = 0; l < B; ++l)
-                if (sh.qi[l] != kEmpty && sh.k[l] >= r) {
-                    act.w[l >> 6] |= 1ull << (l & 63);
-                    if (sh.k[l] > r) last = false;
+            // lanes still running (k >= r) and whether any runs past r, by
+            // ballots over the lane table (lane l = thread l), read by all
+            if (threadIdx.x < B) {
+                const int l = threadIdx.x;
+                const bool on = sh.qi[l] != kEmpty && sh.k[l] >= r;
+                const unsigned ma = __ballot_sync(FULL, on);
+                const unsigned mm = __ballot_sync(FULL, on && sh.k[l] > r);
+                if ((l & 31) == 0) {
+                    s_act[l >> 5] = ma;
+                    s_more[l >> 5] = mm;
                 }
+            }
+            __syncthreads();
+            Lanes<LW> act;
+            bool last = true;
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+                act.w[j] = ((unsigned long long)s_act[2 * j + 1] << 32) | s_act[2 * j];
+                last = last && s_more[2 * j] == 0u && s_more[2 * j + 1] == 0u;
+            }
+            __syncthreads();   // s_act / s_more are rewritten next round
             int dir = DIR_PUSH;
             if (r > 1) {
                 if (prev == DIR_PUSH) dir = fx_gt(mf, a.alpha_fx, a.nnz) ? DIR_PULL : DIR_PUSH;
