@@ -29,8 +29,6 @@ enum { DIR_PUSH = 0, DIR_PULL = 1 };
 constexpr int kBuckets = 64;         // batches are formed per bucket min(k, 63)
 constexpr int kBlock = 512;          // threads per CTA of the batched kernels
 constexpr int kPushUnroll = 4;
-constexpr int kPullILP = 4;          // in-edge loads in flight per lane in a pull round
-constexpr int kLaneEdges = 8;        // in-edges a lane scans alone before the warp helps
 constexpr int kDeferEdges = 4096;    // longer in-lists go to the chunked pass
 constexpr int kChunk = 4096;         // in-edges per chunk of the chunked pass
 constexpr int kPlanes = 4;           // bit-sliced counter planes (up to 15 additions)
@@ -410,6 +408,21 @@ __device__ __forceinline__ Lanes<LW> warp_or(const Lanes<LW> &x) {
     return r;
 }
 
+// Pull-round shape per lane-word width: in-edge loads in flight per lane
+// (ilp) and the in-edges a lane scans alone before the warp helps
+// (lane_edges).  Measured on the scale-21 R-MAT batches: two-word lanes gain
+// most from eight loads in flight, one-word lanes from a longer solo scan.
+template <int LW>
+struct PullShape;
+template <>
+struct PullShape<1> {
+    static constexpr int ilp = 4, lane_edges = 16;
+};
+template <>
+struct PullShape<2> {
+    static constexpr int ilp = 8, lane_edges = 8;
+};
+
 // Pull round, sweep part.  Thread per vertex: need = act & ~V[v] (vertices
 // without in-edges are skipped); the vertex ORs the frontier lanes F_in[u]
 // of its in-neighbours until every needed lane is covered.  A lane first
@@ -421,6 +434,7 @@ template <typename E, int LW>
 __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, Shared<LW> &sh,
                                            uint32_t *st_w, E *st_pre, E *st_d,
                                            unsigned long long *slot) {
+    constexpr int kPullILP = PullShape<LW>::ilp, kLaneEdges = PullShape<LW>::lane_edges;
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
@@ -534,6 +548,7 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Roun
 template <typename E, int LW>
 __device__ __forceinline__ void pull_chunks(const BatchArgs<E, LW> &a, const Round<E, LW> &R,
                                             uint64_t nchunks, Shared<LW> &sh) {
+    constexpr int kPullILP = PullShape<LW>::ilp;
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * kBlock) >> 5;
