@@ -92,10 +92,13 @@ def kernel_source_sha(kernel):
     return h.hexdigest()
 
 
-def captured_traffic(kernel):
+def captured_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on this benchmark's workload, from the
     committed ncu summary profiles/roofline_traffic.md, or None if the kernel's
-    source changed since that capture."""
+    source changed since that capture or the capture was taken on another
+    workload (the summary holds the default scale-21 Kronecker workload)."""
+    if workload != "kronecker21":
+        return None
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     try:
         text = open(path).read()
@@ -260,7 +263,8 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=4096, gname=""):
+def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=4096, gname="",
+                wkey="kronecker21"):
     """The batched multi-source form: nq seeds (seed 2) with k uniform over
     {1,2,3,6}, 64 queries per uint64 lane word, one persistent launch per
     step.  Compared with the plain single-query path on the same queries."""
@@ -370,7 +374,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
             "batches_per_step": st["batches"], "rounds_per_step": st["rounds"],
             "pull_rounds_per_step": st["pull_rounds"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": captured_traffic("batch_kernel"),
+                         "frac": achieved / peak, "traffic": captured_traffic("batch_kernel", wkey),
                          "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"},
             "lanes128": lanes128, "six_hop": six}
 
@@ -677,7 +681,7 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = bytes_sum / t_total / 1e9   # per GPU: one rank's kernel bytes over the max time
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": captured_traffic("plain_kernel"),
+                "frac": achieved / peak, "traffic": captured_traffic("plain_kernel", args.workload),
                 "kernel": "plain_kernel (persistent push/pull traversal)",
                 "peak_kind": peak_kind}
     # per k: the queries' algorithmic bytes over their device-timestamp latencies
@@ -692,7 +696,8 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
-                                        flush, peak, nq=batched_nq, gname=wname.split(" ")[0])
+                                        flush, peak, nq=batched_nq, gname=wname.split(" ")[0],
+                                        wkey=args.workload)
         extras["listing"] = listing_leg(kh, torch, G, g, seeds, ks, ref_counts, dev, stream)
         if args.workload == "kronecker21":
             extras["directions"] = variants_leg(kh, torch, dev, stream, args.scale, args.steps,
@@ -702,7 +707,9 @@ def main():
             if args.workload == "chunglu":
                 g2, _ = workload_graph(21)
                 G2 = kh.Graph.from_csr(g2)
+                # the power-law graph's 6-hop queries take ~1 ms: start the sweep lower
                 extras["serving"] = serving_leg(kh, G, g, mean_by_k, G2=G2, g2=g2,
+                                                rates=(5e3, 10e3, 20e3, 40e3, 80e3),
                                                 names="chunglu-41.6M/1.47e9 and kronecker-s21")
                 G2.close()
             else:
