@@ -180,6 +180,7 @@ struct Shared {
 template <typename E, int LW>
 struct Round {
     bool first, last;
+    bool precheck;               // read V before the atomic (once over 1/32 of n entered)
     Lanes<LW> act;               // lanes still running this round
     const Lanes<LW> *Fin;
     Lanes<LW> *Fout;
@@ -296,14 +297,19 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E, LW> &a, const Rou
 
 // Visit w for the lanes in m: returns true if w entered the union frontier
 // (its first frontier lane this round) and has out-edges; d = out-degree.
-// The degree is read only for that first entry.  In a batch's last round
-// the lanes are ORed in without reading the old bits back (the harvest
-// counts V), so no thread waits on the atomic.
+// The degree is read only for that first entry.  V is read before the
+// atomic only once the union frontier has taken in over 1/32 of the vertices
+// (before that nearly every target is new and the read only lengthens the
+// chain).  In a batch's last round the lanes are ORed in without reading the
+// old bits back (the harvest counts V), so no thread waits on the atomic.
 template <typename E, int LW>
 __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, LW> &R, uint32_t w,
                                       const Lanes<LW> &m, E &d) {
-    const Lanes<LW> x = landnot(m, a.V[w]);
-    if (!lany(x)) return false;
+    Lanes<LW> x = m;
+    if (R.precheck) {
+        x = landnot(m, a.V[w]);
+        if (!lany(x)) return false;
+    }
     if (R.last) {   // the harvest counts V: nothing needs the old bits
         lred_or(&a.V[w], x);
         return false;
@@ -780,6 +786,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
         __syncthreads();
         const uint32_t kmax = sh.kmax;
         uint64_t mf = sh.deg_pre[B], items = B, nf = B;
+        uint64_t entered = B;   // union-frontier entries so far (seeds included)
         int prev = DIR_PUSH;
         for (uint32_t r = 1; r <= kmax && mf > 0; ++r) {
             ++rdone;
@@ -826,6 +833,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
             Round<E, LW> R;
             R.first = r == 1;
             R.last = last;
+            R.precheck = entered * 32 > a.n;
             R.act = act;
             R.Fin = sel3(a.F0, a.F1, a.F2, iin);
             R.Fout = sel3(a.F0, a.F1, a.F2, iout);
@@ -870,6 +878,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
             ++nrounds;
             if (dir == DIR_PULL) ++npull;
             nf = sh.slot[1];
+            entered += nf;
             items = sh.slot[0] >> a.ebits;
             mf = last ? 0 : sh.slot[3];
             prev = dir;

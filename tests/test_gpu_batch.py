@@ -194,3 +194,51 @@ def test_captured_cuda_graph_replays_batched_and_plain():
             np.testing.assert_array_equal(kh.as_u64(out), want)
     assert G.error_bits() == 0
     G.close()
+
+
+def _spread(g, n, seed):
+    """g's vertices relabelled to a seeded sorted sample of range(n)."""
+    ids = np.sort(np.random.default_rng(seed).choice(n, g.n, replace=False)).astype(np.uint32)
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.uint32), deg)
+    return gen.csr_from_edges(n, ids[src], ids[g.col_idx]), ids
+
+
+@pytest.mark.parametrize("mode", LANES)
+def test_sparse_id_space_several_harvest_flushes(mode):
+    """A 4096-vertex R-MAT graph spread over 6M vertex ids: the harvest
+    sweeps every id (dozens of steps per thread, so its bit-sliced counters
+    are summed more than once) and every count still equals the oracle's and
+    the plain path's."""
+    g, ids = _spread(gen.rmat(12, 16, seed=5, symmetrize=True), 6_000_000, seed=6)
+    seeds = gen.seeds(g, 128, seed=7)
+    ks = np.tile(np.array([1, 2, 3, 6], np.uint32), 32)
+    assert check(g, seeds, ks, mode=mode) == 0
+    G = kh.Graph.from_csr(g)
+    plain = G.count_mixed(seeds, ks, mode=kh.MODE_PLAIN)
+    torch.cuda.synchronize()
+    want, _ = oracle.khop_counts(g, seeds, ks)
+    np.testing.assert_array_equal(kh.as_u64(plain), want)
+    G.close()
+
+
+@pytest.mark.parametrize("mode", LANES)
+def test_strided_star_fills_every_counter_plane(mode):
+    """A symmetric star whose leaves are the multiples of 512 in 6M ids: for
+    any grid of 512-thread CTAs a harvest thread meets a leaf at every step,
+    so each lane's counters run through all their planes between flushes."""
+    n = 6_000_000
+    hub = 1
+    leaves = np.arange(0, n, 512, dtype=np.uint32)
+    src = np.concatenate([np.full(leaves.size, hub, np.uint32), leaves])
+    dst = np.concatenate([leaves, np.full(leaves.size, hub, np.uint32)])
+    g = gen.csr_from_edges(n, src, dst)
+    lanes = 64 if mode == kh.MODE_BATCHED64 else 128
+    seeds = np.array([hub] * (lanes // 2) + list(leaves[: lanes // 2]), np.uint32)
+    ks = np.array([1, 2] * (lanes // 4) + [2] * (lanes // 2), np.uint32)
+    want, _ = oracle.khop_counts(g, seeds, ks)
+    assert set(want.tolist()) == {leaves.size}   # hub: its leaves; leaf at k=2: hub + other leaves
+    G = kh.Graph.from_csr(g)
+    np.testing.assert_array_equal(batched(G, seeds, ks, mode), want)
+    assert G.error_bits() == 0
+    G.close()
