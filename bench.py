@@ -337,13 +337,32 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
         raise SystemExit("128-lane counts differ from the 64-lane ones")
     lanes128 = {"value": nq * steps / (sum(ms128) * 1e-3), "unit": "queries/s",
                 "ms_per_step": float(np.mean(ms128)), "mode": "KHOP_MODE_BATCHED128 (direct calls)"}
+    # and 256 per traversal (four lane words per vertex)
+    kh.khop_count_mixed(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_o.data_ptr(),
+                        kh.MODE_BATCHED256, stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms256 = 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kh.khop_count_mixed(G.handle, d_s.data_ptr(), d_k.data_ptr(), nq, d_o.data_ptr(),
+                            kh.MODE_BATCHED256, stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms256 += a.elapsed_time(b)
+    if not np.array_equal(got, kh.as_u64(d_o)):
+        raise SystemExit("256-lane counts differ from the 64-lane ones")
+    lanes256 = {"value": nq * steps / (ms256 * 1e-3), "unit": "queries/s",
+                "ms_per_step": ms256 / steps, "mode": "KHOP_MODE_BATCHED256 (direct calls)"}
     # six-hop traversals alone: 1024 seeds (seed 4) at k = 6, 64 per lane word
     n6 = min(1024, nq)
     s6 = torch.from_numpy(gen.seeds(g, n6, seed=4).view(np.int32)).to(dev)
     k6 = torch.full((n6,), 6, dtype=torch.int32, device=dev)
     o6 = torch.empty(n6, dtype=torch.int64, device=dev)
     six = {"queries": n6}
-    for mode, name in ((kh.MODE_BATCHED64, "lanes64"), (kh.MODE_BATCHED128, "lanes128")):
+    for mode, name in ((kh.MODE_BATCHED64, "lanes64"), (kh.MODE_BATCHED128, "lanes128"),
+                       (kh.MODE_BATCHED256, "lanes256")):
         kh.khop_count_mixed(G.handle, s6.data_ptr(), k6.data_ptr(), n6, o6.data_ptr(), mode,
                             stream.cuda_stream)
         torch.cuda.synchronize()
@@ -376,7 +395,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": captured_traffic("batch_kernel", wkey),
                          "kernel": "batch_kernel (64-lane bit-sliced persistent traversal)"},
-            "lanes128": lanes128, "six_hop": six}
+            "lanes128": lanes128, "lanes256": lanes256, "six_hop": six}
 
 
 K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))

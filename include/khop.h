@@ -174,14 +174,16 @@ enum khop_mode {
     KHOP_MODE_AUTO = 0,       /* batched for nseeds >= 2, else plain              */
     KHOP_MODE_PLAIN = 1,      /* one query at a time                              */
     KHOP_MODE_BATCHED64 = 2,  /* up to 64 queries share one bit-sliced traversal  */
-    KHOP_MODE_BATCHED128 = 3  /* up to 128 queries share one traversal (two lane
+    KHOP_MODE_BATCHED128 = 3, /* up to 128 queries share one traversal (two lane
+                                 words per vertex)                              */
+    KHOP_MODE_BATCHED256 = 4  /* up to 256 queries share one traversal (four lane
                                  words per vertex)                              */
 };
 
 /*
  * Per-seed k (ks[i] for seeds[i]).  In KHOP_MODE_BATCHED64 the queries are
  * grouped by k and packed 64 per uint64 lane word (KHOP_MODE_BATCHED128: 128
- * per pair of words); every lane's result equals the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
+ * per pair of words; KHOP_MODE_BATCHED256: 256 per four words); every lane's result equals the same query run alone.  seeds, ks, out_counts: device arrays of nseeds.
  * After a first call with the same mode on g (which allocates the batch
  * state), khop_count, khop_count_ex and khop_count_mixed issue only stream
  * work, so they may be captured into a CUDA graph and replayed; the graph

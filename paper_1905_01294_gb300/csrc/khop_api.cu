@@ -233,13 +233,13 @@ int khop_count(khop_graph *g, const uint32_t *seeds, uint64_t nseeds, uint32_t k
 int khop_count_mixed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nseeds,
                      uint64_t *out_counts, int mode, void *stream) {
     if (!g) return KHOP_EINVAL;
-    if (mode < KHOP_MODE_AUTO || mode > KHOP_MODE_BATCHED128) return KHOP_EINVAL;
+    if (mode < KHOP_MODE_AUTO || mode > KHOP_MODE_BATCHED256) return KHOP_EINVAL;
     if (nseeds == 0) return KHOP_OK;
     if (!seeds || !ks || !out_counts) return KHOP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool batched = mode == KHOP_MODE_BATCHED64 || mode == KHOP_MODE_BATCHED128 ||
-                         (mode == KHOP_MODE_AUTO && nseeds >= 2);
-    const int lw = mode == KHOP_MODE_BATCHED128 ? 2 : 1;
+                         mode == KHOP_MODE_BATCHED256 || (mode == KHOP_MODE_AUTO && nseeds >= 2);
+    const int lw = mode == KHOP_MODE_BATCHED256 ? 4 : (mode == KHOP_MODE_BATCHED128 ? 2 : 1);
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = order_after_previous(g, st);
     if (rc == KHOP_OK) {
@@ -260,7 +260,7 @@ int khop_batch_stats(khop_graph *g, uint64_t *batches, uint64_t *bytes, uint64_t
     if (!g) return KHOP_EINVAL;
     std::lock_guard<std::mutex> lk(g->mu);
     unsigned long long v[4] = {0, 0, 0, 0};
-    const BatchState &bs = g->last_lw == 2 ? g->batch2 : g->batch;
+    const BatchState &bs = g->last_lw == 4 ? g->batch4 : (g->last_lw == 2 ? g->batch2 : g->batch);
     if (bs.ctl) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = cudaMemcpy(v, bs.ctl->pad, sizeof(v), cudaMemcpyDeviceToHost);

@@ -428,6 +428,10 @@ template <>
 struct PullShape<2> {
     static constexpr int ilp = 8, lane_edges = 8;
 };
+template <>
+struct PullShape<4> {
+    static constexpr int ilp = 8, lane_edges = 8;
+};
 
 // Pull round, sweep part.  Thread per vertex: need = act & ~V[v] (vertices
 // without in-edges are skipped); the vertex ORs the frontier lanes F_in[u]
@@ -700,7 +704,7 @@ __device__ __forceinline__ void harvest(Lanes<LW> *V, uint64_t n, unsigned long 
 template <typename E, int LW>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW> a) {
     constexpr int B = 64 * LW;   // lanes per batch
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    extern __shared__ __align__(32) unsigned char dyn_smem[];
     const uint32_t T2 = (1u << a.tile_log2) + 2u;
     Lanes<LW> *s_fm = (Lanes<LW> *)dyn_smem;                         // [T2]
     E *s_pre = (E *)(s_fm + T2);                                     // [T2]
@@ -995,6 +999,7 @@ BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds,
     uint32_t tl = 0;
     while ((1u << tl) < (uint32_t)g->tune.batch_push_tile) ++tl;
     if (LW == 2 && tl > 12) tl = 12;   // 128 lanes: tiles of at most 4096 edges fit shared memory
+    if (LW == 4 && tl > 11) tl = 11;   // 256 lanes: at most 2048
     a.tile_log2 = tl;
     a.ebits = g->ebits;
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
@@ -1025,7 +1030,7 @@ int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E, LW> &a, int grid_c
 template <typename E, int LW>
 int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st) {
-    BatchState &bs = LW == 2 ? g->batch2 : g->batch;
+    BatchState &bs = LW == 4 ? g->batch4 : (LW == 2 ? g->batch2 : g->batch);
     // order: nq plus up to 64 * LW - 1 padding lanes per bucket
     const uint64_t need = nq + 64ull * LW * kBuckets;
     if (bs.order_cap < need) {
@@ -1061,6 +1066,10 @@ int slot_typed(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *o
 
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st, int lw) {
+    if (lw == 4) {
+        if (g->ewidth == 4) return launch_typed<uint32_t, 4>(g, seeds, ks, nq, out, st);
+        return launch_typed<unsigned long long, 4>(g, seeds, ks, nq, out, st);
+    }
     if (lw == 2) {
         if (g->ewidth == 4) return launch_typed<uint32_t, 2>(g, seeds, ks, nq, out, st);
         return launch_typed<unsigned long long, 2>(g, seeds, ks, nq, out, st);

@@ -271,6 +271,7 @@ void free_graph(khop_graph *g) {
     free_plain_state(g->plain);
     free_batch_state(g->batch);
     free_batch_state(g->batch2);
+    free_batch_state(g->batch4);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
 }
@@ -422,7 +423,7 @@ uint64_t plain_state_bytes(const khop_graph *g) {
 }
 
 int ensure_batch_state(khop_graph *g, int lw) {
-    BatchState &b = lw == 2 ? g->batch2 : g->batch;
+    BatchState &b = lw == 4 ? g->batch4 : (lw == 2 ? g->batch2 : g->batch);
     if (b.V) return KHOP_OK;
     return alloc_batch_state(g, b, nullptr, lw);
 }
@@ -704,14 +705,16 @@ int khop_get_error(khop_graph *g, uint32_t *bits) {
     e = cudaMemcpy(&a, &g->plain.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && g->batch.ctl)
         e = cudaMemcpy(&b, &g->batch.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && g->batch2.ctl) {
-        unsigned b2 = 0;
-        e = cudaMemcpy(&b2, &g->batch2.ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
-        b |= b2;
-    }
+    for (BatchState *w : {&g->batch2, &g->batch4})
+        if (e == cudaSuccess && w->ctl) {
+            unsigned bw = 0;
+            e = cudaMemcpy(&bw, &w->ctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+            b |= bw;
+        }
     if (e == cudaSuccess) e = cudaMemset(&g->plain.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess && g->batch.ctl) e = cudaMemset(&g->batch.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess && g->batch2.ctl) e = cudaMemset(&g->batch2.ctl->err, 0, sizeof(unsigned));
+    if (e == cudaSuccess && g->batch4.ctl) e = cudaMemset(&g->batch4.ctl->err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     *bits = a | b;
     return cuda_status(e);

@@ -291,6 +291,7 @@ struct khop_graph {
 
     khop::BatchState batch;                 // 64 lanes
     khop::BatchState batch2;                // 128 lanes (allocated on first use)
+    khop::BatchState batch4;                // 256 lanes (allocated on first use)
     int last_lw = 1;                        // lane width of the last batched call
 
     khop_tuning tune{};

@@ -29,7 +29,7 @@ HOST_PTRS, DEVICE_PTRS, SYMMETRIC, VALIDATE, WIDE_OFFSETS = 0, 1, 2, 4, 8
 REVERSE, UNDIRECTED = 16, 32
 # directions and modes
 DIR_AUTO, DIR_PUSH, DIR_PULL = 0, 1, 2
-MODE_AUTO, MODE_PLAIN, MODE_BATCHED64, MODE_BATCHED128 = 0, 1, 2, 3
+MODE_AUTO, MODE_PLAIN, MODE_BATCHED64, MODE_BATCHED128, MODE_BATCHED256 = 0, 1, 2, 3, 4
 
 UINT64_MAX = (1 << 64) - 1
 

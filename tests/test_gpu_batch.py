@@ -25,7 +25,8 @@ def _device():
     kh.lib()
 
 
-LANES = [kh.MODE_BATCHED64, kh.MODE_BATCHED128]   # 64 or 128 queries per traversal
+LANES = [kh.MODE_BATCHED64, kh.MODE_BATCHED128, kh.MODE_BATCHED256]   # 64, 128 or 256 queries per traversal
+WIDTH = {kh.MODE_BATCHED64: 64, kh.MODE_BATCHED128: 128, kh.MODE_BATCHED256: 256}
 
 
 def batched(G, seeds, ks, mode=kh.MODE_BATCHED64):
@@ -174,7 +175,7 @@ def test_captured_cuda_graph_replays_batched_and_plain():
     s = torch.from_numpy(seeds.view(np.int32)).cuda()
     k = torch.from_numpy(ks.view(np.int32)).cuda()
     want, _ = oracle.khop_counts(g, seeds, ks)
-    for mode in (kh.MODE_BATCHED64, kh.MODE_BATCHED128, kh.MODE_PLAIN):
+    for mode in (kh.MODE_BATCHED64, kh.MODE_BATCHED128, kh.MODE_BATCHED256, kh.MODE_PLAIN):
         out = torch.zeros(300, dtype=torch.int64, device="cuda")
         side = torch.cuda.Stream()
         with torch.cuda.stream(side):
@@ -233,7 +234,7 @@ def test_strided_star_fills_every_counter_plane(mode):
     src = np.concatenate([np.full(leaves.size, hub, np.uint32), leaves])
     dst = np.concatenate([leaves, np.full(leaves.size, hub, np.uint32)])
     g = gen.csr_from_edges(n, src, dst)
-    lanes = 64 if mode == kh.MODE_BATCHED64 else 128
+    lanes = WIDTH[mode]
     seeds = np.array([hub] * (lanes // 2) + list(leaves[: lanes // 2]), np.uint32)
     ks = np.array([1, 2] * (lanes // 4) + [2] * (lanes // 2), np.uint32)
     want, _ = oracle.khop_counts(g, seeds, ks)
