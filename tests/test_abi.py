@@ -88,3 +88,17 @@ def test_graph_create_without_a_device_fails_loudly(kh):
     assert not out.value
     srv = ctypes.c_void_p()
     assert L.khop_server_create(None, ctypes.byref(srv)) in (kh.ECUDA, kh.ENOMEM)
+
+
+def test_binding_constants_match_the_header(kh):
+    """Every KHOP_* enum value and flag of include/khop.h has the same value
+    under the same name (without the prefix) in the binding."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    pairs = re.findall(r"\b(KHOP_(?:MODE|DIR)_\w+|KHOP_(?:REVERSE|UNDIRECTED|VALIDATE|SYMMETRIC))\s*=\s*(\d+)", src)
+    assert pairs
+    for name, value in pairs:
+        py = name[len("KHOP_"):]
+        assert hasattr(kh, py), py
+        assert getattr(kh, py) == int(value), name
+    modes = {n: int(v) for n, v in pairs if n.startswith("KHOP_MODE_")}
+    assert modes["KHOP_MODE_BATCHED256"] == 4 and len(set(modes.values())) == len(modes)
