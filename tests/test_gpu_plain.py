@@ -202,7 +202,7 @@ def test_fused_first_rounds_at_the_seed_degree_bound():
     rng = np.random.default_rng(91)
     n = 6000
     src, dst = [], []
-    for v, d in ((0, 2048), (1, 2049), (2, 2047), (3, 5), (4, 1)):
+    for v, d in ((0, 2048), (1, 2049), (2, 2047), (3, 5), (4, 1), (5, 1024), (6, 1025), (7, 1023)):
         heads = rng.integers(0, 600, d)     # a dense neighbourhood: many shared heads
         heads[: d // 4] = heads[0]          # duplicate heads
         heads[-1] = v                       # self-loop
@@ -213,8 +213,8 @@ def test_fused_first_rounds_at_the_seed_degree_bound():
     src.append(rng.integers(600, n - 50, 20000))
     dst.append(rng.integers(0, n, 20000))
     g = gen.csr_raw(n, np.concatenate(src), np.concatenate(dst))
-    seeds = np.array([0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 7, 500, n - 1, 5999, 42], np.uint32)
-    ks = np.array([2, 2, 2, 2, 2, 3, 3, 6, 6, 3, 2, 2, 2, 2, 6], np.uint32)
+    seeds = np.array([0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 7, 500, n - 1, 5999, 42, 5, 6, 5, 6], np.uint32)
+    ks = np.array([2, 2, 2, 2, 2, 3, 3, 6, 6, 3, 2, 2, 2, 2, 6, 2, 2, 3, 3], np.uint32)
     check_graph(g, seeds, ks, hop=True)
     check_graph(g, seeds, ks, hop=True, wide=True)
 
