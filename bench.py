@@ -222,8 +222,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    scale = args.scale
-    g, _ = workload_graph(scale)
+    g, wname, _, _ = workload(args)
     seeds, ks = paper_queries(g)
     import oracle
     oracle.build()
@@ -252,7 +251,7 @@ def run_reference(args):
             "value": value, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"kronecker-s{scale}-ef16-sym plain 300/300/10/10 seeds k=1/2/3/6"},
+            "config": {"workload": wname},
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": f"{ss.size} queries per step (1/10 of each k, >= 1), "
                                        "one host thread, scaled to the 620-query mix"},
