@@ -218,6 +218,32 @@ def cpu_baseline(g, seeds, ks, budget_s=25.0):
                       f"{time.time() - t_all:.1f} s; rate weighted by the workload's k mix"}
 
 
+def cpu_pool_baseline(g, seeds, ks, sample):
+    """The oracle as it stands on every host core, one query per thread (a
+    thread pool: the paper's concurrency model for many clients), over the
+    first `sample` queries of the batched workload.  Returns queries/s."""
+    import oracle
+    oracle.build()
+    n = int(min(sample, seeds.size))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.khop_counts(g, seeds[:n], ks[:n], nthreads=cores, with_te=False)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {n} of the batched leg's queries (k mixed), one query per "
+                      f"host thread at a time, {dt:.1f} s"}
+
+
+def push_equivalent_bytes(te, below, width):
+    """Bytes a push-only traversal of the same queries streams (the reference
+    against which a direction choice that saves bytes shows up as speed):
+    per query 4 * TE + (2W + 8) * |{u : dist(s, u) < k}| -- the expanded
+    vertices' edge indices, row offsets and queue entries."""
+    te = np.asarray(te, dtype=np.float64)
+    below = np.asarray(below, dtype=np.float64)
+    return float(np.sum(4.0 * te + (2.0 * width + 8.0) * below))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -698,10 +724,29 @@ def main():
 
     peak, peak_kind = load_peaks()
     achieved = bytes_sum / t_total / 1e9   # per GPU: one rank's kernel bytes over the max time
+    traffic = captured_traffic("plain_kernel", args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": captured_traffic("plain_kernel", args.workload),
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "plain_kernel (persistent push/pull traversal)",
-                "peak_kind": peak_kind}
+                "peak_kind": peak_kind,
+                # the captured DRAM bytes per step over this run's mean step time
+                "dram_gbs": (traffic / (t_total / args.steps) / 1e9) if traffic else None}
+    # push-equivalent bytes: |{u : dist(s, u) < k}| = count(s, k - 1) + 1, from
+    # one untimed plain call at k - 1; TE from the last timed step
+    try:   # an auxiliary figure: the headline line is printed whatever happens here
+        d_kp = torch.from_numpy((np.maximum(ks, 1) - 1).astype(np.uint32).view(np.int32)).to(dev)
+        d_cp = torch.empty(nq, dtype=torch.int64, device=dev)
+        kh.khop_count_mixed(G.handle, d_seeds.data_ptr(), d_kp.data_ptr(), nq, d_cp.data_ptr(),
+                            kh.MODE_PLAIN, stream.cuda_stream)
+        torch.cuda.synchronize()
+        b_ref = push_equivalent_bytes(kh.as_u64(d_te), kh.as_u64(d_cp).astype(np.float64) + 1.0,
+                                      4 if g.nnz < 2**32 else 8)
+        a_ref = b_ref * args.steps / t_total / 1e9
+        roofline["push_equivalent"] = {"bytes_per_step": b_ref, "achieved": a_ref,
+                                       "frac": a_ref / peak}
+    except Exception as exc:   # noqa: BLE001
+        print(f"push-equivalent bytes not computed: {exc}", file=sys.stderr)
+        roofline["push_equivalent"] = None
     # per k: the queries' algorithmic bytes over their device-timestamp latencies
     roofline_by_k = {}
     for k, _ in PAPER_QUERIES:
@@ -756,6 +801,13 @@ def main():
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(g, seeds, ks)
+        if "batched" in line:
+            try:   # an auxiliary baseline: the headline line is printed whatever happens here
+                line["batched"]["cpu_pool"] = cpu_pool_baseline(
+                    g, gen.seeds(g, batched_nq, seed=2), gen.mixed_ks(batched_nq, seed=2),
+                    sample=512 if args.workload == "kronecker21" else 128)
+            except Exception as exc:   # noqa: BLE001
+                print(f"thread-pool oracle baseline not measured: {exc}", file=sys.stderr)
     if rank == 0:
         print(json.dumps(line))
     G.close()

@@ -35,3 +35,32 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_thread_pool_oracle_baseline():
+    import gen
+    b = _bench()
+    g = gen.rmat(12, 16, seed=1, symmetrize=True)
+    r = b.cpu_pool_baseline(g, gen.seeds(g, 256, seed=2), gen.mixed_ks(256, seed=2), sample=64)
+    assert r["value"] > 0 and r["cores"] >= 1 and r["kind"] == "oracle" and "64" in r["sample"]
+
+
+def test_push_equivalent_bytes_closed_form():
+    """A directed path 0 -> 1 -> ... -> 9 from vertex 0 at k = 3 expands
+    vertices 0, 1, 2 (dist < 3) with one out-edge each: 4 * 3 + (2W + 8) * 3."""
+    import gen
+    import oracle
+    b = _bench()
+    g = gen.path_graph(10)
+    c, te = oracle.khop_counts(g, [0], [3])
+    below, _ = oracle.khop_counts(g, [0], [2])
+    got = b.push_equivalent_bytes(te, below.astype(float) + 1.0, 4)
+    assert int(te[0]) == 3 and got == 4 * 3 + (2 * 4 + 8) * 3
