@@ -426,7 +426,7 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
 K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
 
 
-def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=20000,
+def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
                 rates=(25e3, 50e3, 100e3, 200e3, 400e3, 800e3), G2=None, g2=None, names=""):
     """Open-loop Poisson request stream (seed 3), k from {1:.4, 2:.3, 3:.2,
     6:.1}, uniform seeds over out-degree > 0, served by the continuous-
