@@ -35,6 +35,22 @@ def counts_from_reach(R: np.ndarray) -> np.ndarray:
     return R.sum(axis=-1) - diag
 
 
+def per_hop_from_reach(R, k: int) -> np.ndarray:
+    """per_hop[..., s, r] = |{u != s : R_r[s, u] and not R_{r-1}[s, u]}| for
+    r = 1..k (the vertices first reached in r hops, i.e. at distance exactly
+    r), and 1 for r = 0 (the seed itself).  R is the list R_1..R_kmax."""
+    n = R[0].shape[-1]
+    eye = np.eye(n, dtype=bool)
+    out = np.zeros(R[0].shape[:-1] + (k + 1,), dtype=np.int64)
+    out[..., 0] = 1
+    prev = np.broadcast_to(eye, R[0].shape)          # R_0 = {s}
+    for r in range(1, k + 1):
+        cur = R[r - 1] | eye
+        out[..., r] = (cur & ~prev).sum(axis=-1)
+        prev = cur
+    return out
+
+
 def te_from_reach(R_prev, A: np.ndarray, outdeg: np.ndarray) -> np.ndarray:
     """TE(s, k) = sum of outdeg(u) over u = s or R_{k-1}[s, u] (dist < k)."""
     n = A.shape[-1]

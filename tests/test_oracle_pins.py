@@ -62,11 +62,13 @@ def _check_stack(A, kmax, ks):
     outdeg = A.sum(axis=-1)
     seeds = np.arange(G * n, dtype=np.uint32)
     for k in ks:
-        counts, te = oracle.khop_counts(g, seeds, k)
+        counts, te, ph = oracle.khop_counts(g, seeds, k, per_hop=True)
         want = brute.counts_from_reach(R[k - 1]).reshape(-1)
         np.testing.assert_array_equal(counts.astype(np.int64), want)
         want_te = brute.te_from_reach(R[k - 2] if k >= 2 else None, A, outdeg).reshape(-1)
         np.testing.assert_array_equal(te.astype(np.int64), want_te)
+        np.testing.assert_array_equal(ph.astype(np.int64),
+                                      brute.per_hop_from_reach(R, k).reshape(G * n, k + 1))
     c0, t0 = oracle.khop_counts(g, seeds[: 4 * n], 0)
     assert not c0.any() and not t0.any()
 
@@ -97,9 +99,10 @@ def test_random_multigraphs_vs_matrix_powers():
         outdeg = np.diff(g.row_ptr).astype(np.int64)[None]
         seeds = np.arange(n, dtype=np.uint32)
         for k in kset:
-            counts, te = oracle.khop_counts(g, seeds, k)
+            counts, te, ph = oracle.khop_counts(g, seeds, k, per_hop=True)
             np.testing.assert_array_equal(counts.astype(np.int64),
                                           brute.counts_from_reach(R[k - 1])[0])
+            np.testing.assert_array_equal(ph.astype(np.int64), brute.per_hop_from_reach(R, k)[0])
             np.testing.assert_array_equal(
                 te.astype(np.int64),
                 brute.te_from_reach(R[k - 2] if k >= 2 else None, A[None], outdeg)[0])
@@ -172,14 +175,18 @@ def test_rmat_scale10_vs_library_shortest_paths(symmetrize):
     g = gen.rmat(10, 16, seed=1, symmetrize=symmetrize)
     seeds = gen.seeds(g, 64, seed=2)
     outdeg = np.diff(g.row_ptr).astype(np.int64)
+    dists = [_scipy_dist(g, s) for s in seeds]
     for k in (1, 2, 3, 6):
-        counts, te = oracle.khop_counts(g, seeds, k)
+        counts, te, ph = oracle.khop_counts(g, seeds, k, per_hop=True)
         for i, s in enumerate(seeds):
-            d = _scipy_dist(g, s)
+            d = dists[i]
             reach = (d <= k) & np.isfinite(d)
             reach[s] = False
             assert int(counts[i]) == int(reach.sum())
             assert int(te[i]) == int(outdeg[np.isfinite(d) & (d < k)].sum())
+            # per_hop[r] = vertices at library distance exactly r
+            want_ph = [int((d == r).sum()) for r in range(k + 1)]
+            assert ph[i].tolist() == want_ph, (int(s), k)
 
 
 def _components(g):
@@ -247,6 +254,8 @@ MUTANTS = [
     # out-degree of the wrong end: counts edges of vertices at distance <= k
     ("edges += row_ptr[u + 1] - row_ptr[u];\n        for",
      "for"),
+    # per-hop bins shifted: a vertex at distance 2 lands in bin 1
+    ("if (per_hop) per_hop[du + 1]++;", "if (per_hop) per_hop[du == 1 ? 1 : du + 1]++;"),
     # row end taken from the wrong index
     ("for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {\n            uint32_t w = col_idx[e];\n            if (dist[w] == UNSET) {\n                dist[w] = du + 1;",
      "for (uint64_t e = row_ptr[u]; e + 1 < row_ptr[u + 1]; ++e) {\n            uint32_t w = col_idx[e];\n            if (dist[w] == UNSET) {\n                dist[w] = du + 1;"),
