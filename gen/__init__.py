@@ -15,7 +15,10 @@ on first use with gcc into ``libkhopgen.so`` next to this file.
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
 import os
+import shutil
 import subprocess
 import threading
 from dataclasses import dataclass, field
@@ -71,6 +74,8 @@ def _L():
                                                   u64, u64, u64, u64, u32p, u32p, ctypes.c_int]
             lib.khopgen_poisson.argtypes = [u64, ctypes.c_double, u64, ctypes.c_void_p, u32p,
                                             ctypes.c_int, u64, u32p, ctypes.c_void_p, u32p, u32p]
+            lib.khopgen_checksum.restype = u64
+            lib.khopgen_checksum.argtypes = [ctypes.c_void_p, u64, ctypes.c_int]
             lib.khopgen_powerlaw_weights.restype = ctypes.c_double
             lib.khopgen_powerlaw_weights.argtypes = [u64, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_void_p]
@@ -265,6 +270,124 @@ def chunglu(n: int, edges: int, w_max: float, seed: int = 4, nthreads: int = 0,
     params = dict(kind="chunglu", n=n, edges_target=edges, w_max=w_max, w_min=w_min, seed=seed,
                   candidates_drawn=m, prefix_kept=int(mstar.value), edges=int(kept))
     return CSRGraph(n, row_ptr, col[:kept], False, f"chunglu-n{n}-m{edges}-seed{seed}", params)
+
+
+# --------------------------------------------------------------------------
+# On-disk graph cache.  A cached graph is one file:
+#   bytes 0..7     magic b"KHOPCSR1"
+#   bytes 8..15    header length H (uint64, little-endian)
+#   bytes 16..     H bytes of JSON: n, nnz, row_ptr_bytes (8), col_idx_bytes
+#                  (4), symmetric, name, params, the generator's source hash,
+#                  and checksum() of each array
+#   offset 4096*ceil((16 + H) / 4096): row_ptr (uint64[n+1]), then col_idx
+#                  (uint32[nnz])
+# The file name carries a hash of the builder's name, its parameters and the
+# generator sources, so a change to any of them misses the cache.  Loading
+# re-verifies n, nnz, row_ptr[n] = nnz and both checksums; a file that fails
+# is ignored (and rebuilt).
+
+_MAGIC = b"KHOPCSR1"
+_ALIGN = 4096
+
+
+def checksum(a: np.ndarray, nthreads: int = 0) -> int:
+    """64-bit checksum of an array's bytes (khopgen_checksum)."""
+    a = np.ascontiguousarray(a)
+    return int(_L().khopgen_checksum(ctypes.c_void_p(a.ctypes.data), a.nbytes, nthreads))
+
+
+def _generator_hash() -> str:
+    h = hashlib.sha256()
+    for f in (_SRC, os.path.abspath(__file__)):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def cache_dir() -> str:
+    """$KHOP_GRAPH_CACHE, else ~/.cache/khop_graphs."""
+    return os.environ.get("KHOP_GRAPH_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
+                                                             "khop_graphs")
+
+
+def _cache_path(builder: str, params: dict, directory: str | None) -> str:
+    key = json.dumps({"builder": builder, "params": params, "gen": _generator_hash()},
+                     sort_keys=True)
+    tag = hashlib.sha256(key.encode()).hexdigest()[:20]
+    return os.path.join(directory or cache_dir(), f"{builder}-{tag}.csr")
+
+
+def save_graph(g: CSRGraph, path: str) -> bool:
+    """Write g to `path` (atomically: a temporary file, then a rename).
+    Returns False (writing nothing) when the disk lacks room for it."""
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.uint64)
+    ci = np.ascontiguousarray(g.col_idx, dtype=np.uint32)
+    hdr = json.dumps({"n": int(g.n), "nnz": int(g.nnz), "row_ptr_bytes": 8, "col_idx_bytes": 4,
+                      "symmetric": bool(g.symmetric), "name": g.name, "params": g.params,
+                      "generator": _generator_hash(), "checksum_row_ptr": checksum(rp),
+                      "checksum_col_idx": checksum(ci)}, sort_keys=True).encode()
+    off = -(-(16 + len(hdr)) // _ALIGN) * _ALIGN
+    total = off + rp.nbytes + ci.nbytes
+    d = os.path.dirname(path) or "."
+    os.makedirs(d, exist_ok=True)
+    if shutil.disk_usage(d).free < total + (1 << 30):
+        return False
+    tmp = f"{path}.tmp{os.getpid()}"
+    try:
+        with open(tmp, "wb") as f:
+            f.write(_MAGIC)
+            f.write(np.uint64(len(hdr)).tobytes())
+            f.write(hdr)
+            f.write(b"\0" * (off - 16 - len(hdr)))
+            rp.tofile(f)
+            ci.tofile(f)
+        os.replace(tmp, path)
+    except OSError:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+        return False
+    return True
+
+
+def load_graph(path: str) -> CSRGraph | None:
+    """The graph stored at `path`, or None if the file is missing, truncated
+    or fails a check (magic, sizes, row_ptr[n] = nnz, checksums)."""
+    try:
+        with open(path, "rb") as f:
+            if f.read(8) != _MAGIC:
+                return None
+            hlen = int(np.frombuffer(f.read(8), dtype=np.uint64)[0])
+            if hlen > (1 << 20):
+                return None
+            h = json.loads(f.read(hlen))
+            n, nnz = int(h["n"]), int(h["nnz"])
+            if h.get("row_ptr_bytes") != 8 or h.get("col_idx_bytes") != 4:
+                return None
+            off = -(-(16 + hlen) // _ALIGN) * _ALIGN
+            if os.fstat(f.fileno()).st_size != off + 8 * (n + 1) + 4 * nnz:
+                return None
+            f.seek(off)
+            rp = np.fromfile(f, dtype=np.uint64, count=n + 1)
+            ci = np.fromfile(f, dtype=np.uint32, count=nnz)
+    except (OSError, ValueError, KeyError, json.JSONDecodeError):
+        return None
+    if rp.size != n + 1 or ci.size != nnz or int(rp[-1]) != nnz:
+        return None
+    if checksum(rp) != h["checksum_row_ptr"] or checksum(ci) != h["checksum_col_idx"]:
+        return None
+    return CSRGraph(n, rp, ci, bool(h["symmetric"]), h["name"], dict(h["params"]))
+
+
+def cached(builder: str, directory: str | None = None, **params) -> CSRGraph:
+    """gen.<builder>(**params), read from the on-disk cache when a verified
+    copy is there, else built and (room permitting) written to it."""
+    path = _cache_path(builder, params, directory)
+    g = load_graph(path)
+    if g is not None:
+        return g
+    g = globals()[builder](**params)
+    save_graph(g, path)
+    return g
 
 
 def permutation(n: int, key: int) -> np.ndarray:

@@ -580,3 +580,37 @@ void khopgen_chunglu_finish(void *handle, uint64_t *row_ptr, uint32_t *col) {
     pfor(clb_copy, c, c->n, 4096, c->nthreads);
     free(c->deg); free(c->off); free(c->udeg); free(c->kdeg); free(c->hist); free(c->pair); free(c);
 }
+
+/* ------------------------------------------------------------------ */
+/* Checksum of a byte array, for the on-disk graph cache: the sum over  */
+/* 8-byte words w_i (the tail zero-padded) of mix64(w_i ^ mix64(i + 1)), */
+/* mod 2^64, finalised with the byte count.  Order-sensitive through the */
+/* word index, independent of the thread count (the sum commutes).      */
+typedef struct { const unsigned char *p; uint64_t nbytes; uint64_t *part; uint64_t chunk; } ck_ctx;
+
+static void ck_range(void *vc, uint64_t lo, uint64_t hi) {
+    ck_ctx *c = (ck_ctx *)vc;
+    uint64_t acc = 0;
+    for (uint64_t i = lo; i < hi; ++i) {
+        uint64_t w = 0;
+        uint64_t off = i * 8;
+        uint64_t take = c->nbytes - off < 8 ? c->nbytes - off : 8;
+        memcpy(&w, c->p + off, take);
+        acc += mix64(w ^ mix64(i + 1));
+    }
+    c->part[lo / c->chunk] = acc;
+}
+
+uint64_t khopgen_checksum(const void *p, uint64_t nbytes, int nthreads) {
+    const uint64_t words = (nbytes + 7) / 8;
+    const uint64_t chunk = 1ull << 20;
+    const uint64_t nparts = (words + chunk - 1) / chunk;
+    uint64_t *part = (uint64_t *)calloc(nparts ? nparts : 1, sizeof(uint64_t));
+    if (!part) return 0;
+    ck_ctx c = {(const unsigned char *)p, nbytes, part, chunk};
+    pfor(ck_range, &c, words, chunk, nthreads);
+    uint64_t h = 0;
+    for (uint64_t i = 0; i < nparts; ++i) h += part[i];
+    free(part);
+    return mix64(h ^ nbytes);
+}

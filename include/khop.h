@@ -282,16 +282,49 @@ int khop_count_ex(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint
  * calls share the array and the next call overwrites it, so calls whose
  * work overlaps on the GPU (different streams, or different host threads)
  * race: order them on one stream.  Each call resets the state it needs.
- * Errors: EINVAL for sizes beyond the limits or bad pointers, ECUDA.  A seed
- * >= n gives UINT64_MAX (no sticky error word is kept).
+ * The looked-up address belongs to the device's primary context: after
+ * cudaDeviceReset() (or any other destruction of that context) in this
+ * process, the entry point must not be called again on that device.
+ * Errors: EINVAL for sizes beyond the limits or bad pointers, ECUDA.  No
+ * sticky error word is kept: out_counts is first filled with UINT64_MAX and
+ * a query overwrites its entry only when its count is final, so UINT64_MAX
+ * marks a seed >= n or a query whose traversal did not finish (a device wait
+ * that ran out).
  */
 int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint32_t *col_idx,
                       const uint32_t *col_ptr, const uint32_t *row_idx, uint64_t nnz,
                       const uint32_t *seeds, uint64_t nseeds, uint32_t k,
                       uint64_t *out_counts, void *stream);
 
-/* Read and clear the graph's sticky device error bits (synchronises the device). */
+/*
+ * Read and clear the graph's sticky device error bits (synchronises the
+ * device).  After KHOP_DEVERR_TIMEOUT the launch that recorded it stopped
+ * early: the outputs of its unfinished queries are undefined.  The graph
+ * stays usable -- the next call starts from reset traversal state.
+ */
 int khop_get_error(khop_graph *g, uint32_t *device_error_bits);
+
+/*
+ * Bound of every device-side wait of the graph's traversals (the grid
+ * barriers between rounds), in nanoseconds of %globaltimer; 0 restores the
+ * default of 2 s; at most 60 s.  A wait that runs out records
+ * KHOP_DEVERR_TIMEOUT and the launch leaves early instead of hanging.  The
+ * limit must exceed the longest legitimate wait: one round of a traversal,
+ * or, on the plain path, a run of up to 8192 one-CTA 1-hop queries that the
+ * other CTAs wait out at one barrier.  Errors: EINVAL.
+ */
+int khop_graph_set_wait_limit(khop_graph *g, uint64_t timeout_ns);
+
+/*
+ * For testing failure detection without faulting the GPU: in the next
+ * traversal launch on g (plain or batched, then the switch clears itself),
+ * the grid's last CTA does not arrive at its barrier_index-th grid barrier
+ * (1 = the first).  The other CTAs' bounded wait runs out, exactly as if that
+ * CTA had been lost: KHOP_DEVERR_TIMEOUT is recorded and the launch returns;
+ * the absent CTA sleeps until it sees the timeout (at most twice the wait
+ * limit plus 1 ms) and leaves too.  0 switches it off.  Errors: EINVAL.
+ */
+int khop_graph_test_absent_cta(khop_graph *g, uint32_t barrier_index);
 
 /* ---- serving ----------------------------------------------------------- */
 /*

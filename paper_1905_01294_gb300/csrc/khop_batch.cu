@@ -1,4 +1,4 @@
-// Bit-sliced batched k-hop count, 64 * LW lanes (LW = 1 or 2 64-bit words).
+// Bit-sliced batched k-hop count, 64 * LW lanes (LW = 1, 2 or 4 64-bit words).
 //
 // Up to 64 * LW queries share one traversal: every vertex v carries three lane
 // words -- V[v] (lanes that have visited v), F_in[v] / F_out[v] (lanes
@@ -155,6 +155,7 @@ struct BatchArgs {
     int stage;
     uint64_t pull_cap;
     uint64_t timeout_ns;
+    unsigned absent_at;      // testing: the last CTA skips its absent_at-th grid barrier (0 = never)
 };
 
 template <typename T>
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
     // harvest.  A launch that did not finish leaves `dirty` set, and the next
     // one starts from zeroed buffers.  Both words are read before the
     // prologue barrier and written only after it, so every CTA sees the same.
-    unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
+    BarState bsense = barrier_start(&a.ctl->bar, a.absent_at);
     const bool dirty = ld_volatile_u32(&a.ctl->dirty) != 0u;
     uint64_t rdone = dirty ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
     if (gtid < 2ull * B) a.part[gtid] = 0ull;   // the two lane-total rows
@@ -1005,6 +1006,8 @@ BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds,
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
     a.pull_cap = std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.batch_beta) + 32);
     a.timeout_ns = g->timeout_ns;
+    a.absent_at = g->absent_at;   // one launch only
+    g->absent_at = 0;
     return a;
 }
 

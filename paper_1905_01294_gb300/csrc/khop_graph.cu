@@ -720,4 +720,18 @@ int khop_get_error(khop_graph *g, uint32_t *bits) {
     return cuda_status(e);
 }
 
+int khop_graph_set_wait_limit(khop_graph *g, uint64_t timeout_ns) {
+    if (!g || timeout_ns > 60000000000ull) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->timeout_ns = timeout_ns ? timeout_ns : 2000000000ull;
+    return KHOP_OK;
+}
+
+int khop_graph_test_absent_cta(khop_graph *g, uint32_t barrier_index) {
+    if (!g) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->absent_at = barrier_index;
+    return KHOP_OK;
+}
+
 }  // extern "C"

@@ -135,6 +135,27 @@ __device__ __forceinline__ unsigned barrier_sense(const BarrierWords *bw) {
     return v & 0x80000000u;
 }
 
+// What thread 0 of a CTA keeps across the grid barriers of a launch: the
+// sense it expects next, and (for testing failure detection) a countdown:
+// when `absent_left` is non-zero, the CTA does not arrive at its
+// absent_left-th barrier -- it waits for the others to give up instead -- so
+// that their bounded wait runs out the way it would if a CTA were lost.
+struct BarState {
+    unsigned sense;
+    unsigned absent_left;
+};
+
+// Thread 0's state at kernel start: the current sense; the last CTA of the
+// grid gets the countdown `absent_at` (0 = arrive at every barrier).
+__device__ __forceinline__ BarState barrier_start(const BarrierWords *bw, unsigned absent_at) {
+    BarState b{0u, 0u};
+    if (threadIdx.x == 0) {
+        b.sense = barrier_sense(bw);
+        if (blockIdx.x == gridDim.x - 1) b.absent_left = absent_at;
+    }
+    return b;
+}
+
 // Beamer's direction tests (x * c > y, x * c < y for a tuning factor c) in
 // integer arithmetic: c is carried in 1/65536 units and both sides are
 // compared as 128-bit products.  The per-round decisions thus need no FP64,
@@ -162,21 +183,36 @@ struct NoPre {
 
 template <typename Overlap = NoOverlap, typename Pre = NoPre>
 __device__ __forceinline__ bool grid_barrier(BarrierWords *bw, unsigned *err, int *s_flag,
-                                             unsigned &sense,
+                                             BarState &bs,
                                              const unsigned long long *post_src = nullptr,
                                              unsigned long long *post_dst = nullptr,
                                              int post_n = 0, uint64_t timeout_ns = 2000000000ull,
                                              const Overlap &overlap = Overlap(),
                                              const Pre &pre = Pre()) {
     __syncthreads();
+    bool absent = false;
     if (threadIdx.x == 0) {
-        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bw->count), "r"(add)
-                     : "memory");
-        sense ^= 0x80000000u;
+        if (bs.absent_left != 0u && --bs.absent_left == 0u) {
+            absent = true;   // stays away: the others' wait must run out
+        } else {
+            const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bw->count), "r"(add)
+                         : "memory");
+            bs.sense ^= 0x80000000u;
+        }
     }
     pre();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && absent) {
+        // Wait (sleeping) until another CTA records the timeout, bounded by
+        // twice the limit plus a millisecond, then leave like the others.
+        const uint64_t t0 = globaltimer_ns();
+        while (!(ld_volatile_u32(err) & KHOP_DEVERR_TIMEOUT) &&
+               globaltimer_ns() - t0 < 2ull * timeout_ns + 1000000ull)
+            __nanosleep(1000);
+        atomicOr(err, (unsigned)KHOP_DEVERR_TIMEOUT);
+        *s_flag = 0;
+    } else if (threadIdx.x == 0) {
+        const unsigned sense = bs.sense;
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
         uint64_t spins = 0;
@@ -295,7 +331,8 @@ struct khop_graph {
     int last_lw = 1;                        // lane width of the last batched call
 
     khop_tuning tune{};
-    uint64_t timeout_ns = 2000000000ull;
+    uint64_t timeout_ns = 2000000000ull;   // bound of every device wait (grid barriers)
+    unsigned absent_at = 0;                // testing: see khop_graph_test_absent_cta
     uint64_t device_bytes = 0;
 
     std::mutex mu;
@@ -332,7 +369,7 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                        uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st);
 
-// batched path (khop_batch.cu); lw = 1 (64 lanes) or 2 (128 lanes per traversal)
+// batched path (khop_batch.cu); lw = 1, 2 or 4 (64, 128 or 256 lanes per traversal)
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st, int lw = 1);
 // One batch of up to 64 lanes on a standalone state.  `lanes` (device,

@@ -72,6 +72,7 @@ struct PlainArgs {
     int stage;               // stage queue items per CTA (needs nnz < 2^40)
     uint64_t pull_cap;       // queue items a pull round writes (enough for a switch back to push)
     uint64_t timeout_ns;
+    unsigned absent_at;      // testing: the last CTA skips its absent_at-th grid barrier (0 = never)
 };
 
 template <typename T>
@@ -854,7 +855,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         sh.qfull = 0;
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
-    unsigned bsense = threadIdx.x == 0 ? barrier_sense(&a.ctl->bar) : 0u;
+    BarState bsense = barrier_start(&a.ctl->bar, a.absent_at);
     if (threadIdx.x == 0) sh.ring_q = ~0ull;
     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
         s_nbr[i] = kHashEmpty;
@@ -1188,6 +1189,8 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
                      ? 0ull
                      : std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.beta) + 32);
     a.timeout_ns = g->timeout_ns;
+    a.absent_at = g->absent_at;   // one launch only
+    g->absent_at = 0;
     const size_t smem = plain_smem_bytes<E>(tl);
     switch (g->tune.block_threads) {
         case 256: return launch_block<E, 256>(g, a, smem, grid_ctas, st);
@@ -1253,7 +1256,9 @@ std::mutex g_static_mu;
 uint32_t *g_static_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (set up once
-// per device, with that device current).
+// per device, with that device current).  The address is kept for the life
+// of the process: it belongs to the device's primary context, so it does not
+// survive cudaDeviceReset() or any other destruction of that context.
 int static_scratch(uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1355,6 +1360,7 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     a.stage = 1;
     a.pull_cap = has_csc ? std::min<uint64_t>(n, (uint64_t)std::ceil((double)n / 24.0) + 32) : 0ull;
     a.timeout_ns = 2000000000ull;
+    a.absent_at = 0;
 
     static_noin_kernel<<<nsm * 4, 256, 0, st>>>(col_ptr, n, nw, noin);
     e = cudaGetLastError();
@@ -1368,6 +1374,11 @@ extern "C" int khop_count_static(uint64_t n, const uint32_t *row_ptr, const uint
     rc = cooperative_grid(fn, kBlk, smem, 2, nsm, &grid);
     if (rc != KHOP_OK) return rc;
     e = cudaMemsetAsync(a.ctl, 0, sizeof(CtlBlock), st);   // counters, barrier and error word
+    if (e != cudaSuccess) return cuda_status(e);
+    // No error word survives the call, so a query the kernel does not finish
+    // (a grid barrier that gave up) must not leave stale memory behind: every
+    // count starts as UINT64_MAX and only a finished query overwrites it.
+    e = cudaMemsetAsync(out_counts, 0xff, nseeds * sizeof(uint64_t), st);
     if (e != cudaSuccess) return cuda_status(e);
     void *args[] = {(void *)&a};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlk), args, smem, st);

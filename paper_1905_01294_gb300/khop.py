@@ -40,7 +40,7 @@ EXPORTS = [
     "khop_count", "khop_count_mixed", "khop_count_ex", "khop_count_static", "khop_get_error",
     "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list", "khop_levels",
     "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
-    "khop_server_destroy",
+    "khop_server_destroy", "khop_graph_set_wait_limit", "khop_graph_test_absent_cta",
 ]
 
 
@@ -108,6 +108,8 @@ def lib():
                 "khop_count_ex": (i32, [vp, vp, vp, u64, vp, vp, vp, vp, u32, vp]),
                 "khop_count_static": (i32, [u64, vp, vp, vp, vp, u64, vp, u64, u32, vp, vp]),
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
+                "khop_graph_set_wait_limit": (i32, [vp, u64]),
+                "khop_graph_test_absent_cta": (i32, [vp, u32]),
                 "khop_neighbourhood": (i32, [vp, u32, u32, vp, vp, vp]),
                 "khop_neighbourhood_list": (i32, [vp, u32, u32, vp, u64, vp, vp]),
                 "khop_levels": (i32, [vp, u32, u32, vp, vp, vp]),
@@ -224,6 +226,14 @@ def khop_get_error(g) -> int:
     bits = ctypes.c_uint32()
     check(lib().khop_get_error(g, ctypes.byref(bits)), "khop_get_error")
     return bits.value
+
+
+def khop_graph_set_wait_limit(g, timeout_ns) -> None:
+    check(lib().khop_graph_set_wait_limit(g, timeout_ns), "khop_graph_set_wait_limit")
+
+
+def khop_graph_test_absent_cta(g, barrier_index) -> None:
+    check(lib().khop_graph_test_absent_cta(g, barrier_index), "khop_graph_test_absent_cta")
 
 
 def khop_batch_stats(g):
@@ -366,6 +376,12 @@ class Graph:
 
     def error_bits(self) -> int:
         return khop_get_error(self.handle)
+
+    def set_wait_limit(self, timeout_ns: int) -> None:
+        khop_graph_set_wait_limit(self.handle, int(timeout_ns))
+
+    def test_absent_cta(self, barrier_index: int) -> None:
+        khop_graph_test_absent_cta(self.handle, int(barrier_index))
 
     # counting
     def _u32(self, x):

@@ -10,17 +10,22 @@ KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "
         "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e")
 
 
-def _run(env_extra):
+def _run(env_extra, wall=None):
+    import time
     env = dict(os.environ, **env_extra)
+    t0 = time.time()
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--scale", "12",
                         "--steps", "2", "--warmup", "1"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=300)
+    if wall is not None:
+        wall.append(time.time() - t0)
     assert r.returncode == 0, r.stderr[-2000:]
     return [ln for ln in r.stdout.splitlines() if ln.strip()]
 
 
 def test_reference_arm_prints_one_contract_line():
-    lines = _run({})
+    wall = []
+    lines = _run({}, wall)
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference"
@@ -31,6 +36,18 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the timed region really ran: every query of each step, inside the process's lifetime
+    assert d["config"]["queries_per_step"] == 620
+    assert d["steps"] * d["ms_per_step"] * 1e-3 < wall[0]
+    assert abs(d["value"] - 620 / (d["ms_per_step"] * 1e-3)) < 1e-6 * d["value"]
+    # the same config object as the GPU arm prints for this workload
+    b = _bench()
+    assert set(d["config"]) == set(b.workload_config("w", _G(), 620, 1))
+
+
+def _G():
+    import gen
+    return gen.path_graph(3)
 
 
 def test_reference_arm_other_ranks_print_nothing():

@@ -137,3 +137,43 @@ def test_chunglu_graph_valid_deterministic_and_sized():
     ind = np.bincount(g.col_idx, minlength=g.n)
     assert 0.5 * 3000 < outd.max() < 3000 * 1.3 and 0.5 * 3000 < ind.max() < 3000 * 1.3
     assert np.corrcoef(outd, ind)[0, 1] < 0.1      # independent out/in weights
+
+
+# ---- on-disk graph cache -----------------------------------------------------
+
+def test_checksum_is_order_sensitive_and_thread_independent():
+    a = np.arange(1000003, dtype=np.uint32)
+    c1 = gen.checksum(a, nthreads=1)
+    assert c1 == gen.checksum(a, nthreads=7)
+    b = a.copy()
+    b[[10, 11]] = b[[11, 10]]                    # swap two entries
+    assert gen.checksum(b) != c1
+    assert gen.checksum(a[:-1]) != c1            # length matters
+    assert gen.checksum(np.zeros(3, np.uint8)) != gen.checksum(np.zeros(4, np.uint8))
+
+
+def test_graph_cache_round_trip_and_rejects_damage(tmp_path):
+    g = gen.cached("rmat", directory=str(tmp_path), scale=9, edge_factor=8, seed=3)
+    files = list(tmp_path.glob("rmat-*.csr"))
+    assert len(files) == 1
+    h = gen.cached("rmat", directory=str(tmp_path), scale=9, edge_factor=8, seed=3)
+    assert h.n == g.n and h.params == g.params
+    np.testing.assert_array_equal(h.row_ptr, g.row_ptr)
+    np.testing.assert_array_equal(h.col_idx, g.col_idx)
+    ref = gen.rmat(9, 8, seed=3)
+    np.testing.assert_array_equal(h.col_idx, ref.col_idx)
+    # other parameters miss the cache
+    gen.cached("rmat", directory=str(tmp_path), scale=9, edge_factor=8, seed=4)
+    assert len(list(tmp_path.glob("rmat-*.csr"))) == 2
+    # one flipped byte in the edge array, or a truncated file, fails the checks
+    path = str(files[0])
+    raw = bytearray(open(path, "rb").read())
+    raw[-3] ^= 0x40
+    open(path, "wb").write(bytes(raw))
+    assert gen.load_graph(path) is None
+    open(path, "wb").write(bytes(raw[:-4]))
+    assert gen.load_graph(path) is None
+    # and the next cached() call rebuilds a good copy
+    k = gen.cached("rmat", directory=str(tmp_path), scale=9, edge_factor=8, seed=3)
+    np.testing.assert_array_equal(k.col_idx, ref.col_idx)
+    assert gen.load_graph(path) is not None

@@ -302,21 +302,27 @@ def test_stats_are_consistent():
     G.close()
 
 
-def test_scale21_symmetric_sampled_in_bench_configuration():
-    """The benchmark workload: Kronecker scale 21, edge factor 16, symmetrized,
-    in the launch configuration the benchmark times; sampled seeds against the
-    oracle (the full 300/300/10/10 seed lists are checked by the benchmark's
-    own verification)."""
+def test_scale21_paper_protocol_in_bench_configuration():
+    """The benchmark workload -- Kronecker scale 21, edge factor 16,
+    symmetrized -- in the launch configuration the benchmark times: the
+    graph autotuned on the benchmark's tuning sample (1024 seeds of stream 9,
+    k mixed over {1,2,3,6}), then all 620 paper-protocol queries (300/300/10/10
+    seeds at k = 1/2/3/6) in one khop_count_ex launch.  Every count, TE and
+    per-hop count equals the oracle's."""
+    import bench
     g = gen.rmat(21, 16, seed=1, symmetrize=True)
     G = kh.Graph.from_csr(g)
-    seeds = gen.seeds(g, 300, seed=2)
-    for k, idx in ((1, slice(0, 300, 10)), (2, slice(0, 300, 25)), (3, slice(0, 10)),
-                   (6, slice(0, 10))):
-        s = seeds[idx]
-        got = gpu_counts(G, s, k)
-        want, want_te = oracle.khop_counts(g, s, k)
-        np.testing.assert_array_equal(got["counts"], want)
-        np.testing.assert_array_equal(got["te"], want_te)
+    G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    seeds, ks = bench.paper_queries(g)
+    assert seeds.size == 620
+    want_c, want_te, want_ph = oracle.khop_counts(g, seeds, ks, per_hop=True)
+    stride = want_ph.shape[1]
+    res = G.count_ex(seeds, ks, te=True, hop_stride=stride)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(kh.as_u64(res["counts"]), want_c)
+    np.testing.assert_array_equal(kh.as_u64(res["te"]), want_te)
+    ph = kh.as_u64(res["per_hop"]).reshape(seeds.size, stride)
+    np.testing.assert_array_equal(ph, want_ph)     # bins beyond a query's k are 0 on both sides
     assert G.error_bits() == 0
     G.close()
 

@@ -4,18 +4,24 @@ It serves callers that cannot allocate device memory (their memory belongs to
 another allocator, or they cannot take an allocation's implicit device
 synchronisation), so it keeps its traversal state in a fixed device array and
 takes the graph as raw device arrays.  Its counts must equal those of
-khop_count on a graph created the usual way, on two calls in a row (the second
-call reuses the state the first one left behind).
+khop_count on a graph created the usual way and the oracle's, on two calls in
+a row (the second call reuses the state the first one left behind), with a
+separate CSC, with the CSR passed again as the CSC of a symmetric graph, and
+without a CSC (push only).  A seed >= n gives UINT64_MAX.
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 kh = pytest.importorskip("paper_1905_01294_gb300")
+
+
+U64MAX = np.uint64(2**64 - 1)
 
 
 def _dev_u32(a):
@@ -36,23 +42,34 @@ def test_static_entry_point_matches_khop_count_twice(symmetric):
     g = gen.rmat(14, 16, seed=11, symmetrize=symmetric)
     G = kh.Graph.from_csr(g)
     seeds = gen.seeds(g, 96, seed=12)
+    seeds[5] = g.n + 3                          # out of range: UINT64_MAX
     d_seeds = _dev_u32(seeds)
     rp, ci = _dev_u32(g.row_ptr), _dev_u32(g.col_idx)
     cp_h, ri_h = _csc(g)
     cp, ri = _dev_u32(cp_h), _dev_u32(ri_h)
     stream = torch.cuda.current_stream().cuda_stream
-    for k in (6, 2):                         # two calls in a row
-        want = kh.as_u64(G.count(seeds, k))
-        out = torch.empty(seeds.size, dtype=torch.int64, device="cuda")
-        kh.khop_count_static(g.n, rp.data_ptr(), ci.data_ptr(), cp.data_ptr(), ri.data_ptr(),
-                             g.nnz, d_seeds.data_ptr(), seeds.size, k, out.data_ptr(), stream)
-        torch.cuda.synchronize()
-        np.testing.assert_array_equal(kh.as_u64(out), want)   # counts are integers: exact
+    # the CSC as separate arrays; for the symmetric graph also the CSR arrays
+    # passed again as the CSC (the entry point's declared-symmetric branch)
+    cscs = [(cp, ri)] + ([(rp, ci)] if symmetric else [])
+    for k in (6, 2):                         # two calls in a row, each CSC form
+        want, _ = oracle.khop_counts(g, seeds, k)
+        assert want[5] == U64MAX
+        ref = kh.as_u64(G.count(seeds, k))
+        np.testing.assert_array_equal(ref, want)
+        for c_p, r_i in cscs:
+            out = torch.empty(seeds.size, dtype=torch.int64, device="cuda")
+            kh.khop_count_static(g.n, rp.data_ptr(), ci.data_ptr(), c_p.data_ptr(), r_i.data_ptr(),
+                                 g.nnz, d_seeds.data_ptr(), seeds.size, k, out.data_ptr(), stream)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(kh.as_u64(out), want)   # integers: exact
+            np.testing.assert_array_equal(kh.as_u64(out), ref)
     # push-only form (no CSC) agrees as well
     out = torch.empty(seeds.size, dtype=torch.int64, device="cuda")
     kh.khop_count_static(g.n, rp.data_ptr(), ci.data_ptr(), None, None, g.nnz,
                          d_seeds.data_ptr(), seeds.size, 3, out.data_ptr(), stream)
     torch.cuda.synchronize()
+    want, _ = oracle.khop_counts(g, seeds, 3)
+    np.testing.assert_array_equal(kh.as_u64(out), want)
     np.testing.assert_array_equal(kh.as_u64(out), kh.as_u64(G.count(seeds, 3)))
     G.close()
 
