@@ -456,12 +456,15 @@ K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
 
 
 def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
-                rates=(25e3, 50e3, 100e3, 200e3, 400e3, 800e3), G2=None, g2=None, names=""):
+                rates=(25e3, 50e3, 100e3, 150e3, 200e3, 300e3, 400e3), G2=None, g2=None, names=""):
     """Open-loop Poisson request stream (seed 3), k from {1:.4, 2:.3, 3:.2,
     6:.1}, uniform seeds over out-degree > 0, served by the continuous-
-    batching server; the arrival rate rises until the server saturates.
-    With a second resident graph, a seeded fair coin sends each request to
-    one of the two.  Latency = completion time - scheduled arrival time."""
+    batching server; the arrival rate rises until the server saturates
+    (achieves less than 0.9 of the offered rate).  With a second resident
+    graph, a seeded fair coin sends each request to one of the two.
+    Latency = completion time - scheduled arrival time.  `value` is the best
+    achieved rate; latency is also reported at the highest offered rate the
+    server sustained."""
     plain_rate = 1.0 / sum(p * plain_mean_us_by_k[k] * 1e-6 for k, p in K_MIX)
     points, checked = [], False
     for rate in rates:
@@ -471,7 +474,7 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
             on2 = (gen.rand_array(gen.subkey(3, 11), 0, nreq) >> np.uint64(63)).astype(bool)
             _, _, sd2 = gen.poisson_stream(g2, nreq, rate, seed=5, k_probs=K_MIX)
             sd = np.where(on2, sd2, sd).astype(np.uint32)
-        srv = kh.Server(max_batches=8)
+        srv = kh.Server()
         srv.submit_many(G, sd[:256][~on2[:256]], ks[:256][~on2[:256]])   # warm-up: slots allocated
         if G2 is not None:
             srv.submit_many(G2, sd[:256][on2[:256]], ks[:256][on2[:256]])
@@ -504,6 +507,7 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
             x = srv.poll_arrays(8192, 100000)
             done.append(x)
             ndone += len(x)
+        counters = srv.counters()
         srv.close()
         res = np.concatenate(done)
         res = res[np.argsort(res["ticket"])]
@@ -520,15 +524,23 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
             if not np.array_equal(res["count"], alone):
                 raise SystemExit("serving: a served count differs from the query alone")
             checked = True
-        pt = {"offered_qps": rate, "achieved_qps": nreq / span, "latency_us": percentiles(lat_us)}
+        pt = {"offered_qps": rate, "achieved_qps": nreq / span, "latency_us": percentiles(lat_us),
+              "latency_us_by_k": {str(k): percentiles(lat_us[ks == k]) for k, _ in K_MIX},
+              "server": {k: v for k, v in counters.items()
+                         if k in ("steps", "joined_running", "plain_launches", "pull_steps",
+                                  "slots_allocated", "max_lanes_busy")}}
         points.append(pt)
         if pt["achieved_qps"] < 0.9 * rate:
             break
     best = max(points, key=lambda x: x["achieved_qps"])
+    held = [p for p in points if p["achieved_qps"] >= 0.9 * p["offered_qps"]]
+    top = max(held, key=lambda x: x["offered_qps"]) if held else None
     return {"workload": f"{names} resident, open-loop Poisson (seed 3), "
                         f"{nreq} requests per rate, k ~ {{1:.4, 2:.3, 3:.2, 6:.1}}",
             "value": best["achieved_qps"], "unit": "queries/s",
-            "latency_us_at_best": best["latency_us"],
+            "sustained_qps": top["achieved_qps"] if top else None,
+            "latency_us_at_sustained": top["latency_us"] if top else None,
+            "latency_us_at_sustained_offered_qps": top["offered_qps"] if top else None,
             "plain_sequential_same_mix_qps": plain_rate,
             "speedup_vs_plain": best["achieved_qps"] / plain_rate,
             "sweep": points}
@@ -801,7 +813,7 @@ def main():
                 G2 = kh.Graph.from_csr(g2)
                 # the power-law graph's 6-hop queries take ~1 ms: start the sweep lower
                 extras["serving"] = serving_leg(kh, G, g, mean_by_k, G2=G2, g2=g2,
-                                                rates=(5e3, 10e3, 20e3, 40e3, 80e3),
+                                                rates=(5e3, 10e3, 20e3, 40e3, 80e3, 160e3),
                                                 names="chunglu-41.6M/1.47e9 and kronecker-s21")
                 G2.close()
             else:

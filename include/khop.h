@@ -329,21 +329,37 @@ int khop_graph_test_absent_cta(khop_graph *g, uint32_t barrier_index);
 /* ---- serving ----------------------------------------------------------- */
 /*
  * A request server: k-hop queries of mixed k arrive one by one on resident
- * graphs and are continuously batched: at every round boundary free lanes of
- * the 64-lane bit-sliced batches take waiting requests, each lane keeps its
- * own round counter, and a lane retires (its count is final) after its k-th
- * round.  Batch state is admitted by free device memory.  This is the GPU
- * counterpart of the paper's thread pool serving many concurrent queries at
- * low latency (Sec. II).
+ * graphs.  Heavy requests (k >= 3) are continuously batched at round
+ * granularity: a rolling slot holds a 64-lane bit-sliced traversal on the
+ * device and runs it one round per step (one launch); a step advances every
+ * lane in use by one hop, whatever its depth.  Between steps a worker thread
+ * posts the result of every lane the step retired -- its k-th round ran, or
+ * its frontier came out empty, so its count is final -- and admits waiting
+ * requests into the free lanes, each with its own round counter: a request
+ * that arrives while a traversal runs joins it at the next round boundary.
+ * Light requests (k <= 2) take a few microseconds each on the single-query
+ * path, so plain slots answer them in arrival order, several per launch.
+ * Slots (their device state) are admitted by free device memory and the
+ * budget; the launches of different slots run side by side on the device.
+ * This is the GPU counterpart of the paper's thread pool serving many
+ * concurrent queries at low latency (Sec. II).
  */
 typedef struct khop_server khop_server;
 
 typedef struct {
-    uint64_t mem_budget_bytes;   /* max device bytes for batch state (0 = no cap
+    uint64_t mem_budget_bytes;   /* max device bytes for slot state (0 = no cap
                                     beyond free memory minus a 1 GiB margin)   */
-    uint32_t max_batches;        /* max 64-lane batches per graph (0 = 8)       */
-    int64_t wait_timeout_us;     /* bound for the worker's device waits (0 = 2 s) */
+    uint32_t max_batches;        /* max rolling 64-lane slots per graph (0 = 2;
+                                    at most 2)                                   */
+    int64_t wait_timeout_us;     /* bound for the worker's wait for a step
+                                    (0 = 2 s; negative: EINVAL)                 */
     uint32_t max_pending;        /* max queued requests before EBUSY (0 = 1<<20) */
+    uint32_t admit_rounds;       /* a rolling traversal admits new lanes while its
+                                    lanes have run at most this many rounds
+                                    (0 = 1; UINT32_MAX = at every step)          */
+    int32_t plain_heavy;         /* heavy requests take the single-query path
+                                    while at most this many wait (0 = 2;
+                                    negative = never)                            */
 } khop_server_opts;
 
 typedef struct {
@@ -380,9 +396,39 @@ int khop_submit_many(khop_server *s, khop_graph *g, const uint32_t *seeds, const
  */
 int khop_poll(khop_server *s, khop_result *out, uint32_t max, uint32_t *nout, int64_t timeout_us);
 
-/* Server counters (any pointer may be NULL). */
+/* Server counters (any pointer may be NULL); batches_allocated = rolling slots allocated. */
 int khop_server_stats(khop_server *s, uint64_t *submitted, uint64_t *completed,
                       uint64_t *steps, uint64_t *batches_allocated);
+
+typedef struct {
+    uint64_t submitted;        /* requests accepted by khop_submit / khop_submit_many  */
+    uint64_t completed;        /* results posted (any status)                          */
+    uint64_t steps;            /* step launches (one round of one slot each)           */
+    uint64_t slots_allocated;  /* slots whose device state was admitted               */
+    uint64_t joined_running;   /* requests admitted into a slot whose traversal was
+                                  already running (continuous batching)               */
+    uint64_t retired_early;    /* lanes retired before their k-th round: the frontier
+                                  came out empty                                      */
+    uint64_t timed_out;        /* requests completed with KHOP_ETIMEDOUT              */
+    uint64_t max_lanes_busy;   /* most lanes in use at once, over all slots           */
+    uint64_t gpu_step_ns;      /* device time of the steps (sum of their durations)   */
+    uint64_t pull_steps;       /* steps whose round ran as a pull                    */
+    uint64_t clean_steps;      /* steps asked to sweep retired lanes' marks away      */
+    uint64_t lane_steps;       /* sum over steps of the lanes they advanced           */
+    uint64_t plain_launches;   /* launches of the single-query path (light requests)  */
+} khop_server_counters;
+
+/* All server counters at once.  Errors: EINVAL. */
+int khop_server_counters_get(khop_server *s, khop_server_counters *out);
+
+/*
+ * Change the bound of the worker's wait for a step (the options' 
+ * wait_timeout_us; 0 = 2 s) for the steps launched from now on.  A step still
+ * running past the bound is given up: the requests it held complete with
+ * KHOP_ETIMEDOUT at once, and its slot is reused from zeroed state once the
+ * step has finished.  Errors: EINVAL (NULL server, negative bound).
+ */
+int khop_server_set_wait_timeout(khop_server *s, int64_t wait_timeout_us);
 
 /* Stop the worker; requests not finished are completed with ESHUTDOWN. */
 int khop_server_destroy(khop_server *s);

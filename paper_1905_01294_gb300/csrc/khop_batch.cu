@@ -156,6 +156,9 @@ struct BatchArgs {
     uint64_t pull_cap;
     uint64_t timeout_ns;
     unsigned absent_at;      // testing: the last CTA skips its absent_at-th grid barrier (0 = never)
+    uint32_t *S0, *S1;       // rolling batch: discovered vertices without out-edges, per round
+                             // parity (null otherwise); with the queue they list every non-zero
+                             // F_out entry
 };
 
 template <typename T>
@@ -168,7 +171,7 @@ struct Shared {
     unsigned long long cnt, mf, stage, limit, gbase, scan, unv;
     unsigned long long skipped;  // items not queued because the queue was past its cap
     int qfull;                   // this CTA saw the queue past its cap (pull rounds)
-    unsigned long long slot[8];
+    unsigned long long slot[16];
     int flag;
     // lane table of the current batch
     uint32_t seed[64 * LW];
@@ -193,6 +196,8 @@ struct Round {
     uint32_t *TF_out;
     unsigned long long *qpack_out;
     uint64_t cap, items_in, mf;
+    unsigned long long clean;    // one-word lanes: retired lanes whose V marks a pull sweep clears
+    uint32_t *S_out;             // rolling batch: sink list of this round (or null)
 };
 
 template <typename E, int LW>
@@ -262,6 +267,21 @@ __device__ __forceinline__ void record(const BatchArgs<E, LW> &a, const Round<E,
     }
 }
 
+// Warp-collective: lanes with `is` append their vertex w to the round's sink
+// list (rolling batches only; one global atomic per warp).
+template <typename E, int LW>
+__device__ __forceinline__ void sink_record(const BatchArgs<E, LW> &a, const Round<E, LW> &R, bool is,
+                                            uint32_t w) {
+    const unsigned m = __ballot_sync(FULL, is);
+    if (m == 0u || R.S_out == nullptr) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&((RoundSlot *)R.qpack_out)->sinks, (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    const uint64_t pos = base + (uint64_t)__popc(m & lanemask_lt());
+    if (is && pos < a.n) R.S_out[pos] = w;
+}
+
 template <typename E, int LW>
 __device__ __forceinline__ void flush_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, Shared<LW> &sh,
                                             uint32_t *st_w, E *st_pre, E *st_d,
@@ -305,7 +325,7 @@ __device__ __forceinline__ void flush_round(const BatchArgs<E, LW> &a, const Rou
 // old bits back (the harvest counts V), so no thread waits on the atomic.
 template <typename E, int LW>
 __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, LW> &R, uint32_t w,
-                                      const Lanes<LW> &m, E &d) {
+                                      const Lanes<LW> &m, E &d, Lanes<LW> &seen, bool &sink) {
     Lanes<LW> x = m;
     if (R.precheck) {
         x = landnot(m, a.V[w]);
@@ -317,6 +337,7 @@ __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, 
     }
     const Lanes<LW> nb = landnot(x, latomic_or(&a.V[w], x));
     if (!lany(nb)) return false;
+    lor_into(seen, nb);   // these lanes discovered a vertex this round
     // entry into the union frontier: a word of F_out[w] this call turned from
     // zero to non-zero.  With one word that is exactly one caller per vertex;
     // with LW words up to LW callers may queue w (extra work, same counts),
@@ -327,6 +348,7 @@ __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, 
     for (int j = 0; j < LW; ++j) entered = entered || (nb.w[j] != 0ull && of.w[j] == 0ull);
     if (!entered) return false;
     d = a.rp[w + 1] - a.rp[w];
+    sink = d == 0;
     return d > 0;
 }
 
@@ -336,7 +358,8 @@ __device__ __forceinline__ bool visit(const BatchArgs<E, LW> &a, const Round<E, 
 template <typename E, int LW>
 __device__ __forceinline__ void push_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, E *s_pre,
                                            E *s_rs, Lanes<LW> *s_fm, uint32_t *s_u,
-                                           Shared<LW> &sh, uint32_t *st_w, E *st_pre, E *st_d) {
+                                           Shared<LW> &sh, uint32_t *st_w, E *st_pre, E *st_d,
+                                           Lanes<LW> &seen) {
     const uint32_t tl = a.tile_log2;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
@@ -393,8 +416,10 @@ __device__ __forceinline__ void push_round(const BatchArgs<E, LW> &a, const Roun
 #pragma unroll
             for (int u = 0; u < kPushUnroll; ++u) {
                 E d = 0;
-                const bool isnew = lany(m[u]) && visit(a, R, w[u], m[u], d);
+                bool sink = false;
+                const bool isnew = lany(m[u]) && visit(a, R, w[u], m[u], d, seen, sink);
                 record(a, R, isnew, w[u], d, sh, st_w, st_pre, st_d);
+                if (R.S_out) sink_record(a, R, sink, w[u]);
             }
         }
         __syncthreads();
@@ -444,7 +469,7 @@ struct PullShape<4> {
 template <typename E, int LW>
 __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Round<E, LW> &R, Shared<LW> &sh,
                                            uint32_t *st_w, E *st_pre, E *st_d,
-                                           unsigned long long *slot) {
+                                           unsigned long long *slot, Lanes<LW> &seen) {
     constexpr int kPullILP = PullShape<LW>::ilp, kLaneEdges = PullShape<LW>::lane_edges;
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -453,14 +478,19 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Roun
     for (uint64_t i = gwarp; i < a.nw; i += nwarps) {
         const uint64_t v = (i << 5) + (uint64_t)lane;
         const uint32_t ni = a.noin[i];
+        Lanes<LW> vv0 = lzero<LW>();
+        if (v < a.n && !((ni >> lane) & 1u)) {
+            vv0 = a.V[v];
+            if (LW == 1 && (vv0.w[0] & R.clean)) {   // retired lanes' marks, cleared in passing
+                vv0.w[0] &= ~R.clean;
+                a.V[v] = vv0;
+            }
+        }
         Lanes<LW> need = lzero<LW>();
-        if (v < a.n && !((ni >> lane) & 1u)) need = landnot(R.act, a.V[v]);
+        if (v < a.n && !((ni >> lane) & 1u)) need = landnot(R.act, vv0);
         const bool needs = lany(need);
         const unsigned nmask = __ballot_sync(FULL, needs);
-        if (nmask == 0u) {
-            if (v < a.n) R.Fout[v] = lzero<LW>();
-            continue;
-        }
+        if (nmask == 0u) continue;   // F_out was zeroed one round ahead
         unv += __popc(nmask);
         E b = 0, e = 0;
         if (needs) {
@@ -534,17 +564,17 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Roun
         }
         const Lanes<LW> nb = defer ? lzero<LW>() : land(acc, need);
         const bool any_nb = lany(nb);
-        if (v < a.n) {
+        lor_into(seen, nb);
+        if (v < a.n && any_nb) {
             R.Fout[v] = nb;
-            if (any_nb) {
-                Lanes<LW> vv = a.V[v];
-                lor_into(vv, nb);
-                a.V[v] = vv;
-            }
+            Lanes<LW> vv = vv0;
+            lor_into(vv, nb);
+            a.V[v] = vv;
         }
         E d = 0;
         if (any_nb && !R.last) d = a.symmetric ? e - b : a.rp[v + 1] - a.rp[v];
         record(a, R, any_nb && d > 0, (uint32_t)v, d, sh, st_w, st_pre, st_d);
+        if (R.S_out) sink_record(a, R, any_nb && d == 0, (uint32_t)v);
     }
     scanned = warp_sum(scanned);
     if (lane == 0) {
@@ -600,7 +630,7 @@ __device__ __forceinline__ void pull_chunks(const BatchArgs<E, LW> &a, const Rou
 template <typename E, int LW>
 __device__ __forceinline__ void pull_settle(const BatchArgs<E, LW> &a, const Round<E, LW> &R,
                                             uint64_t nitems, Shared<LW> &sh, uint32_t *st_w,
-                                            E *st_pre, E *st_d) {
+                                            E *st_pre, E *st_d, Lanes<LW> &seen) {
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
     const uint64_t iters = (nitems + gthreads - 1) / gthreads;   // uniform: record() is warp-wide
@@ -613,6 +643,7 @@ __device__ __forceinline__ void pull_settle(const BatchArgs<E, LW> &a, const Rou
             v = a.hv[h];
             nb = land(a.hacc[h], a.hneed[h]);
             a.hacc[h] = lzero<LW>();
+            lor_into(seen, nb);
             R.Fout[v] = nb;
             if (lany(nb)) {
                 Lanes<LW> vv = a.V[v];
@@ -622,6 +653,7 @@ __device__ __forceinline__ void pull_settle(const BatchArgs<E, LW> &a, const Rou
             }
         }
         record(a, R, lany(nb) && d > 0, v, d, sh, st_w, st_pre, st_d);
+        if (R.S_out) sink_record(a, R, lany(nb) && d == 0, v);
     }
 }
 
@@ -852,10 +884,13 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
             R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
             R.items_in = items;
             R.mf = mf;
+            R.clean = 0ull;
+            R.S_out = nullptr;
+            Lanes<LW> seen_unused = lzero<LW>();   // only the rolling kernel reads it
             if (dir == DIR_PUSH)
-                push_round<E, LW>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d);
+                push_round<E, LW>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d, seen_unused);
             else {
-                pull_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+                pull_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout, seen_unused);
                 // deferred long in-lists (counts read after a barrier: uniform)
                 if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout + 5,
                                   sh.slot + 5, 2, a.timeout_ns))
@@ -866,20 +901,23 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
                     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0,
                                       a.timeout_ns))
                         return;
-                    pull_settle<E, LW>(a, R, nitems, sh, st_w, st_pre, st_d);
+                    pull_settle<E, LW>(a, R, nitems, sh, st_w, st_pre, st_d, seen_unused);
                 }
             }
             flush_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot, 5,
                               a.timeout_ns))
                 return;
-            const uint64_t W = sizeof(E), LB = 8ull * LW;   // LB: bytes of a lane word
-            const uint64_t items_out = last ? 0 : min((uint64_t)(sh.slot[0] >> a.ebits), R.cap);
+            // Algorithmic bytes (LB: bytes of a lane word): push: per frontier
+            // vertex 2W row offsets + its lane word, per out-edge 4 + LB (edge
+            // index, lane-word update); pull: LB n (visited sweep) + LB n (next
+            // frontier) + 2W per vertex examined + (4 + LB) per in-edge scanned
+            // (index, frontier gather).
+            const uint64_t W = sizeof(E), LB = 8ull * LW;
             if (dir == DIR_PUSH)
-                bytes += items * (4 + 2 * W + LB) + (4 + LB) * R.mf + items_out * (4 + W);
+                bytes += items * (2 * W + LB) + (4 + LB) * R.mf;
             else
-                bytes += 2 * LB * a.n + 4ull * a.nw + 2 * W * sh.slot[4] + (4 + LB) * sh.slot[2] +
-                         items_out * (4 + W);
+                bytes += 2 * LB * a.n + 2 * W * sh.slot[4] + (4 + LB) * sh.slot[2];
             ++nrounds;
             if (dir == DIR_PULL) ++npull;
             nf = sh.slot[1];
@@ -891,7 +929,6 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
         // harvest the lane counts, clear V: every CTA adds its lane counts
         // into the row of this batch's parity; CTA 0 reads the totals after
         // the barrier and zeroes the row for batch b + 2.
-        bytes += 16ull * LW * a.n;
         unsigned long long *row = a.part + (b & 1) * (uint64_t)B;
         harvest<LW>(a.V, a.n, row, s_lane);
         if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
@@ -910,6 +947,383 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs<E, LW>
         a.ctl->rdone = rdone;
         __threadfence();
         a.ctl->dirty = 0u;
+    }
+}
+
+// ===========================================================================
+// Rolling 64-lane batch: continuous batching at round granularity.
+//
+// A request server keeps one traversal state per slot and runs it one round
+// per launch ("step").  Lanes are independent bit positions, so lanes at
+// different depths share a round: the round computes
+//     F_out[w] = (OR over edges u -> w of F_in[u]) AND NOT V[w] AND act
+// for every active lane at once, each advancing its own q_r by one hop.  A
+// step (1) admits new requests into free lanes -- lane l with seed s gets
+// V[s] |= l and F_in[s] |= l (its q_0 = {s}), and s joins the union-frontier
+// queue unless it is in it already -- (2) runs one push or pull round for the
+// active lanes, (3) counts each lane's discoveries of the round, retires the
+// lanes whose k is reached or whose frontier came out empty (their counts are
+// final) and zeroes the frontier buffer the round consumed.
+//
+// Every step's cost follows its frontier, not n: the queue and the sink list
+// (discovered vertices without out-edges) together list every vertex whose
+// F_out entry the round set, so the discoveries are counted and the spent F_in
+// zeroed by walking them.  Only a pull round whose queue overflowed (more
+// discoveries than a switch back to push would take) leaves its buffer
+// "dense", handled by full sweeps.  F entries are never cleared bit by bit
+// (an entry is non-zero exactly when its vertex is listed), so a retired
+// lane's bits stay in the next frontier, masked off by `act`, until that
+// buffer is zeroed one round later; the host reuses the lane after that.  Its
+// visited marks are cleared lazily: the next pull round (which reads V of
+// every vertex with in-edges) clears them in passing, its seed's mark is
+// cleared at once, and a step asked for a dense clean sweeps V.  The state
+// between steps -- queue size, out-edges, union frontier, direction, which
+// buffers are dense, the lanes' seeds and running counts -- stays on the
+// device.
+
+// Control-block words the rolling state keeps between steps.
+enum { RS_MF = 0, RS_ITEMS, RS_NF, RS_ENTERED, RS_PREV, RS_DEAD, RS_DENSE, RS_NSINK, RS_WORDS };
+
+// The vertices whose F entry a round set: its queue Q[0..nq) then its sink
+// list S[0..ns) -- or, when `dense` (the queue overflowed), all n vertices.
+struct Listed {
+    const uint32_t *Q, *S;
+    uint64_t nq, ns;
+    bool dense;
+    __device__ __forceinline__ uint64_t total(uint64_t n) const { return dense ? n : nq + ns; }
+    __device__ __forceinline__ uint64_t at(uint64_t x) const {
+        return dense ? x : (x < nq ? (uint64_t)Q[x] : (uint64_t)S[x - nq]);
+    }
+};
+
+// Per-lane bit counts of F over the listed vertices, added into row[64]
+// (bit-sliced planes as in harvest()); with `zero`, the entries are zeroed
+// after they are read.
+__device__ __forceinline__ void roll_count(Lanes<1> *F, const Listed &L, uint64_t n, bool zero,
+                                           unsigned long long *row, unsigned *s_lane) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 64) s_lane[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint64_t total = L.total(n);
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t iters = (total + gthreads - 1) / gthreads;   // uniform across the grid
+    unsigned long long p[kPlanes];
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) p[i] = 0ull;
+    for (uint64_t it = 0; it < iters; ++it) {
+        const uint64_t x = gtid + it * gthreads;
+        unsigned long long y = 0ull;
+        if (x < total) {
+            const uint64_t w = L.at(x);
+            y = F[w].w[0];
+            if (zero && y) F[w].w[0] = 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < kPlanes; ++i) {   // ripple-carry add of y into the planes
+            const unsigned long long c = p[i] & y;
+            p[i] ^= y;
+            y = c;
+        }
+        if ((it + 1) % ((1u << kPlanes) - 1u) == 0 || it + 1 == iters) {
+            unsigned long long q[kSumPlanes];
+#pragma unroll
+            for (int i = 0; i < kSumPlanes; ++i) q[i] = i < kPlanes ? p[i] : 0ull;
+#pragma unroll
+            for (int lv = 0; lv < 5; ++lv) {   // q += q of lane ^ 2^lv
+                unsigned long long c = 0ull;
+#pragma unroll
+                for (int i = 0; i < kSumPlanes; ++i) {
+                    if (i > kPlanes + lv) break;
+                    const unsigned long long o = __shfl_xor_sync(FULL, q[i], 1 << lv);
+                    const unsigned long long t = q[i] ^ o;
+                    const unsigned long long cn = (q[i] & o) | (c & t);
+                    q[i] = t ^ c;
+                    c = cn;
+                }
+            }
+            unsigned lo = 0, hi = 0;
+#pragma unroll
+            for (int i = 0; i < kSumPlanes; ++i) {
+                lo |= (unsigned)((q[i] >> lane) & 1ull) << i;
+                hi |= (unsigned)((q[i] >> (lane + 32)) & 1ull) << i;
+            }
+#pragma unroll
+            for (int i = 0; i < kPlanes; ++i) p[i] = 0ull;
+            if (lo) atomicAdd(&s_lane[lane], lo);
+            if (hi) atomicAdd(&s_lane[lane + 32], hi);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && s_lane[threadIdx.x])
+        atomicAdd(row + threadIdx.x, (unsigned long long)s_lane[threadIdx.x]);
+}
+
+// Zero F at the listed vertices.
+__device__ __forceinline__ void roll_zero(Lanes<1> *F, const Listed &L, uint64_t n) {
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t total = L.total(n);
+    for (uint64_t x = gtid; x < total; x += gthreads) F[L.at(x)].w[0] = 0ull;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kBlock, 2) roll_kernel(const BatchArgs<E, 1> a, const RollPlan plan,
+                                                        RollResult *res) {
+    constexpr int LW = 1;
+    extern __shared__ __align__(32) unsigned char dyn_smem[];
+    const uint32_t T2 = (1u << a.tile_log2) + 2u;
+    Lanes<LW> *s_fm = (Lanes<LW> *)dyn_smem;                         // [T2]
+    E *s_pre = (E *)(s_fm + T2);                                     // [T2]
+    E *s_rs = s_pre + T2;                                            // [T2]
+    uint32_t *s_u = (uint32_t *)(s_rs + T2);                         // [T2]
+    uint32_t *st_w = s_u + T2;                                       // [kStage]
+    E *st_pre = (E *)(st_w + kStage);                                // [kStage]
+    E *st_d = st_pre + kStage;                                       // [kStage]
+    __shared__ Shared<LW> sh;
+    __shared__ unsigned s_lane[64];
+    __shared__ unsigned long long s_seen;
+    __shared__ unsigned long long s_st[RS_WORDS];
+
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    unsigned long long *slots = (unsigned long long *)a.ctl->slot;
+    unsigned long long *hs = a.ctl->handoff;   // RS_* words
+    unsigned long long *total = a.part;        // [64] running count of each lane
+    unsigned long long *lseed = a.part + 64;   // [64] seed of each lane in use
+    const uint64_t t_start = (blockIdx.x == 0 && threadIdx.x == 0) ? globaltimer_ns() : 0ull;
+    if (threadIdx.x == 0) {
+        sh.cnt = sh.mf = sh.stage = sh.scan = sh.unv = 0;
+        sh.limit = ~0ull;
+        sh.skipped = 0;
+        sh.qfull = 0;
+        s_seen = 0ull;
+    }
+    BarState bsense = barrier_start(&a.ctl->bar, a.absent_at);
+    // A step that did not finish leaves `dirty` set; the host asks for a reset
+    // after it gave a step up.  Either way the state starts from zero.
+    const bool fresh = plan.reset != 0u || ld_volatile_u32(&a.ctl->dirty) != 0u;
+    uint64_t rdone = fresh ? 0ull : *(volatile unsigned long long *)&a.ctl->rdone;
+    if (fresh) {
+        for (uint64_t v = gtid; v < a.n; v += gthreads) {
+            a.V[v] = lzero<LW>();
+            a.F0[v] = lzero<LW>();
+            a.F1[v] = lzero<LW>();
+            a.F2[v] = lzero<LW>();
+        }
+        if (gtid < 128) a.part[gtid] = 0ull;
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns))
+            return;
+    } else if (plan.clean_dense && plan.clean) {
+        // the retired lanes' visited marks, everywhere (admission below only
+        // sets bits of other lanes, so both may run at once)
+        for (uint64_t v = gtid; v < a.n; v += gthreads)
+            if (a.V[v].w[0] & plan.clean) atomicAnd(&a.V[v].w[0], ~plan.clean);
+    }
+    // (1) admission, by the first warp of CTA 0: new lanes into V, F_in and
+    // the union-frontier queue the round reads.
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long st[RS_WORDS];
+#pragma unroll
+        for (int i = 0; i < RS_WORDS; ++i) st[i] = fresh ? 0ull : hs[i];
+        Lanes<LW> *Fin = sel3(a.F0, a.F1, a.F2, (unsigned)(rdone % 3));
+        Round<E, LW> R;
+        R.Q_out = (rdone & 1) ? a.Q1 : a.Q0;
+        R.Qpre_out = (rdone & 1) ? a.Qpre1 : a.Qpre0;
+        R.TF_out = (rdone & 1) ? a.TF1 : a.TF0;
+        R.cap = a.n;
+        unsigned long long dead = 0ull;
+        for (uint32_t base = 0; base < plan.nadmit; base += 32) {
+            const uint32_t t = base + (uint32_t)lane;
+            const bool on = t < plan.nadmit && t < 64u;
+            const uint32_t l = on ? plan.lane[t] & 63u : 0u, s = on ? plan.seed[t] : 0u;
+            E d = 0;
+            bool ni = false;
+            if (on) {
+                d = a.rp[s + 1] - a.rp[s];
+                const unsigned long long bit = 1ull << l;
+                total[l] = 0ull;
+                lseed[l] = s;
+                if (d == 0) {
+                    dead |= bit;
+                } else {
+                    atomicOr(&a.V[s].w[0], bit);
+                    ni = atomicOr(&Fin[s].w[0], bit) == 0ull;   // s enters the union frontier
+                }
+            }
+            const E dd = ni ? d : (E)0;
+            const E incl = warp_inclusive_sum(dd);
+            const unsigned m = __ballot_sync(FULL, ni);
+            if (ni)
+                put_item(a, R, st[RS_ITEMS] + (uint64_t)__popc(m & lanemask_lt()),
+                         st[RS_MF] + (uint64_t)(incl - dd), s, d);
+            st[RS_ITEMS] += (unsigned long long)__popc(m);
+            st[RS_MF] += (unsigned long long)__shfl_sync(FULL, incl, 31);
+            st[RS_NF] += (unsigned long long)__popc(m);
+            st[RS_ENTERED] += (unsigned long long)__popc(m);
+        }
+        dead = warp_or64(dead);
+        if (lane == 0) {
+            st[RS_DEAD] = dead;
+#pragma unroll
+            for (int i = 0; i < RS_WORDS; ++i) hs[i] = st[i];
+        }
+    }
+    if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, hs, s_st, RS_WORDS, a.timeout_ns)) return;
+    if (gtid == 0) a.ctl->dirty = 1u;
+    uint64_t mf = s_st[RS_MF], items = s_st[RS_ITEMS], nf = s_st[RS_NF], entered = s_st[RS_ENTERED];
+    int prev = (int)s_st[RS_PREV];
+    const unsigned long long dead = s_st[RS_DEAD];
+    unsigned dense = (unsigned)s_st[RS_DENSE];       // bit b: F buffer b is not listed by its queue
+    const unsigned long long act = plan.act & ~dead;
+    // (2) one round for the active lanes
+    const bool run = act != 0ull && mf > 0;
+    const uint64_t items_in = items, nsink_in = s_st[RS_NSINK];
+    uint64_t nsink_out = 0;
+    unsigned long long seen_all = 0ull, bytes = 0ull, pulled = 0ull;
+    bool cleaned = plan.clean_dense != 0u;
+    if (run) {
+        ++rdone;
+        const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
+        const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
+        // Direction.  A pull exits a vertex's in-list early only once every
+        // lane that still needs the vertex is covered, and lanes that joined
+        // recently (small frontiers) almost never are: with lanes at widely
+        // mixed depths a pull scans nearly every in-edge.  So a rolling batch
+        // pushes unless the plan allows Beamer's switch (the host allows it
+        // when its lanes' depths are close); a queue that overflowed in a
+        // pull forces the next round to pull too.
+        int dir = DIR_PUSH;
+        if (prev == DIR_PULL && items > a.pull_cap) dir = DIR_PULL;
+        else if (plan.pull_ok) {
+            if (prev == DIR_PUSH) dir = fx_gt(mf, a.alpha_fx, a.nnz) ? DIR_PULL : DIR_PUSH;
+            else dir = (fx_lt(nf, a.beta_fx, a.n) && items <= a.pull_cap) ? DIR_PUSH : DIR_PULL;
+        }
+        // (the round's counter slot was zeroed with the control block at launch)
+        Round<E, LW> R;
+        R.first = false;
+        R.last = false;
+        R.precheck = entered * 32 > a.n;
+        R.act.w[0] = act;
+        R.Fin = sel3(a.F0, a.F1, a.F2, iin);
+        R.Fout = sel3(a.F0, a.F1, a.F2, iout);
+        R.Q_in = qin ? a.Q1 : a.Q0;
+        R.Qpre_in = qin ? a.Qpre1 : a.Qpre0;
+        R.TF_in = qin ? a.TF1 : a.TF0;
+        R.Q_out = qout ? a.Q1 : a.Q0;
+        R.Qpre_out = qout ? a.Qpre1 : a.Qpre0;
+        R.TF_out = qout ? a.TF1 : a.TF0;
+        R.qpack_out = slots + kSlotWords * iout;
+        R.cap = dir == DIR_PUSH ? a.n : a.pull_cap;
+        R.items_in = items;
+        R.mf = mf;
+        R.clean = dir == DIR_PULL ? plan.clean : 0ull;
+        R.S_out = qout ? a.S1 : a.S0;
+        Lanes<LW> seen = lzero<LW>();
+        if (dir == DIR_PUSH) {
+            push_round<E, LW>(a, R, s_pre, s_rs, s_fm, s_u, sh, st_w, st_pre, st_d, seen);
+        } else {
+            pull_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout, seen);
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout + 5,
+                              sh.slot + 5, 2, a.timeout_ns))
+                return;
+            const uint64_t nitems = min((uint64_t)sh.slot[5], a.hcap);
+            if (nitems) {
+                pull_chunks<E, LW>(a, R, min((uint64_t)sh.slot[6], a.ccap), sh);
+                if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0,
+                                  a.timeout_ns))
+                    return;
+                pull_settle<E, LW>(a, R, nitems, sh, st_w, st_pre, st_d, seen);
+            }
+        }
+        const unsigned long long sw = warp_or64(seen.w[0]);
+        if ((threadIdx.x & 31) == 0 && sw) atomicOr(&s_seen, sw);
+        flush_round<E, LW>(a, R, sh, st_w, st_pre, st_d, slots + kSlotWords * iout);
+        if (threadIdx.x == 0 && s_seen) atomicOr(slots + kSlotWords * iout + 7, s_seen);
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot, 9,
+                          a.timeout_ns))
+            return;
+        const uint64_t W = sizeof(E), LB = 8ull;
+        if (dir == DIR_PUSH) {
+            bytes = items * (2 * W + LB) + (4 + LB) * mf;
+        } else {
+            bytes = 2 * LB * a.n + 2 * W * sh.slot[4] + (4 + LB) * sh.slot[2];
+            pulled = 1ull;
+            cleaned = true;   // the sweep read V of every vertex with in-edges
+        }
+        seen_all = sh.slot[7];
+        nsink_out = sh.slot[8];
+        nf = sh.slot[1];
+        entered += nf;
+        const uint64_t counted = sh.slot[0] >> a.ebits;   // queue entries of the round (stored or not)
+        items = counted;
+        mf = sh.slot[3];
+        prev = dir;
+        // the output buffer is listed by its queue unless the queue overflowed
+        if (counted > R.cap) dense |= 1u << iout;
+        else dense &= ~(1u << iout);
+    }
+    // (3) retire: k reached, or nothing discovered this round (the lane's
+    // frontier is empty, so its count is final), or a seed without out-edges
+    const unsigned long long retire = (plan.fin & act) | (act & ~seen_all) | dead;
+    const bool idle = (act & ~retire) == 0ull;   // no lane continues: the next step starts clean
+    if (run) {
+        const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
+        const unsigned pin = (unsigned)((rdone - 1) & 1), pout = (unsigned)(rdone & 1);
+        const Listed Lout{pout ? a.Q1 : a.Q0, pout ? a.S1 : a.S0, items, nsink_out, ((dense >> iout) & 1u) != 0u};
+        const Listed Lin{pin ? a.Q1 : a.Q0, pin ? a.S1 : a.S0, items_in, nsink_in, ((dense >> iin) & 1u) != 0u};
+        // the round's discoveries per lane (and, with no lane left, the buffer
+        // is zeroed on the way); the consumed frontier is zeroed (it is
+        // written again two rounds on)
+        roll_count(sel3(a.F0, a.F1, a.F2, iout), Lout, a.n, idle, total, s_lane);
+        roll_zero(sel3(a.F0, a.F1, a.F2, iin), Lin, a.n);
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns))
+            return;
+    } else if (idle && (items_in || nsink_in)) {
+        // no round ran and no lane continues: zero the frontier the next round would read
+        const unsigned icur = (unsigned)(rdone % 3), pcur = (unsigned)(rdone & 1);
+        const Listed Lcur{pcur ? a.Q1 : a.Q0, pcur ? a.S1 : a.S0, items_in, nsink_in, ((dense >> icur) & 1u) != 0u};
+        roll_zero(sel3(a.F0, a.F1, a.F2, icur), Lcur, a.n);
+        if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns))
+            return;
+    }
+    if (run) dense &= ~(1u << (unsigned)((rdone - 1) % 3));
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x < 64) {
+        const int l = threadIdx.x;
+        if ((retire >> l) & 1ull) {
+            res->count[l] = total[l];
+            total[l] = 0ull;
+            if (!((dead >> l) & 1ull)) {   // its seed's mark goes now, the rest lazily
+                const uint64_t sd = lseed[l];
+                atomicAnd(&a.V[sd].w[0], ~(1ull << l));
+            }
+        }
+    }
+    __syncthreads();   // the counts are written before `done`
+    if (threadIdx.x == 0) {
+        hs[RS_MF] = idle ? 0ull : mf;
+        hs[RS_ITEMS] = idle ? 0ull : items;
+        hs[RS_NF] = idle ? 0ull : nf;
+        hs[RS_ENTERED] = idle ? 0ull : entered;
+        hs[RS_PREV] = idle ? (unsigned long long)DIR_PUSH : (unsigned long long)prev;
+        hs[RS_DEAD] = 0ull;
+        hs[RS_DENSE] = idle ? 0ull : dense;   // no lane left: every buffer is zero
+        hs[RS_NSINK] = idle ? 0ull : (run ? nsink_out : nsink_in);
+        a.ctl->rdone = rdone;
+        res->retired = retire;
+        res->cleaned = cleaned ? plan.clean : 0ull;
+        res->rdone = rdone;
+        res->idle = idle ? 1ull : 0ull;
+        res->union_nf = nf;
+        res->bytes = bytes;
+        res->pulled = pulled;
+        res->t_start_ns = t_start;
+        res->t_end_ns = globaltimer_ns();
+        __threadfence_system();
+        a.ctl->dirty = 0u;
+        res->done = 1ull;
     }
 }
 
@@ -959,7 +1373,8 @@ __global__ void __launch_bounds__(1024) group_kernel(const uint32_t *seeds, cons
 // Kernel arguments over a batch state.
 template <typename E, int LW>
 BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds, const uint32_t *ks,
-                           uint64_t *out, const uint32_t *order, const unsigned long long *nbatches) {
+                           uint64_t *out, const uint32_t *order, const unsigned long long *nbatches,
+                           bool take_test_switch = true) {
     BatchArgs<E, LW> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -1006,8 +1421,13 @@ BatchArgs<E, LW> make_args(khop_graph *g, BatchState &bs, const uint32_t *seeds,
     a.stage = g->nnz < (1ull << kStagePosShift) ? 1 : 0;
     a.pull_cap = std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.batch_beta) + 32);
     a.timeout_ns = g->timeout_ns;
-    a.absent_at = g->absent_at;   // one launch only
-    g->absent_at = 0;
+    a.S0 = bs.S[0];
+    a.S1 = bs.S[1];
+    a.absent_at = 0;
+    if (take_test_switch) {
+        a.absent_at = g->absent_at;   // one launch only
+        g->absent_at = 0;
+    }
     return a;
 }
 
@@ -1018,11 +1438,10 @@ int launch_kernel(khop_graph *g, BatchState &bs, BatchArgs<E, LW> &a, int grid_c
     const size_t T2 = (size_t(1) << a.tile_log2) + 2;
     const size_t smem = T2 * (8 * LW + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
     const void *fn = (const void *)batch_kernel<E, LW>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
     int grid = 0;
-    int rc = cooperative_grid(fn, kBlock, smem, 0, g->num_sms, &grid);
+    int rc = launch_shape(fn, kBlock, smem, 0, g->num_sms, &grid);
     if (rc != KHOP_OK) return rc;
+    cudaError_t e;
     if (grid_ctas > 0 && grid_ctas < grid) grid = grid_ctas;
     if ((uint64_t)grid > bs.part_rows) return KHOP_EINVAL;
     void *args[] = {(void *)&a};
@@ -1055,17 +1474,38 @@ int launch_typed(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     return launch_kernel<E, LW>(g, bs, a, 0, st);
 }
 
+
 template <typename E>
-int slot_typed(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
-               int grid_ctas, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, err), st);
+int roll_typed(khop_graph *g, BatchState &bs, const RollPlan &plan, RollResult *res, int grid_ctas,
+               cudaStream_t st) {
+    if (bs.lw != 1) return KHOP_EINVAL;
+    BatchArgs<E, 1> a = make_args<E, 1>(g, bs, nullptr, nullptr, nullptr, nullptr, nullptr, false);
+    if (!a.S0 || !a.S1) return KHOP_EINVAL;   // a rolling state has sink lists
+    const size_t T2 = (size_t(1) << a.tile_log2) + 2;
+    const size_t smem = T2 * (8 + 2 * sizeof(E) + 4) + kStage * (4 + 2 * sizeof(E));
+    const void *fn = (const void *)roll_kernel<E>;
+    int grid = 0;
+    int rc = launch_shape(fn, kBlock, smem, 0, g->num_sms, &grid);
+    if (rc != KHOP_OK) return rc;
+    if (grid_ctas > 0 && grid_ctas < grid) grid = grid_ctas;
+    if ((uint64_t)grid > bs.part_rows) return KHOP_EINVAL;
+    // counters, barrier word (the rolling state lives in `handoff`, `rdone`, `dirty`)
+    cudaError_t e = cudaMemsetAsync(bs.ctl, 0, offsetof(CtlBlock, handoff), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&bs.ctl->bar, 0, sizeof(BarrierWords), st);
     if (e != cudaSuccess) return cuda_status(e);
-    BatchArgs<E, 1> a = make_args<E, 1>(g, bs, lanes, lanes + 64, out, lanes + 128,
-                                        (const unsigned long long *)(lanes + 192));
-    return launch_kernel<E, 1>(g, bs, a, grid_ctas, st);
+    RollPlan p = plan;
+    void *args[] = {(void *)&a, (void *)&p, (void *)&res};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, st);
+    return cuda_status(e);
 }
 
 }  // namespace
+
+int roll_launch(khop_graph *g, BatchState &bs, const RollPlan &plan, RollResult *res, int grid_ctas,
+                cudaStream_t st) {
+    if (g->ewidth == 4) return roll_typed<uint32_t>(g, bs, plan, res, grid_ctas, st);
+    return roll_typed<unsigned long long>(g, bs, plan, res, grid_ctas, st);
+}
 
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st, int lw) {
@@ -1081,10 +1521,5 @@ int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint6
     return launch_typed<unsigned long long, 1>(g, seeds, ks, nq, out, st);
 }
 
-int batch_launch_slot(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
-                      int grid_ctas, cudaStream_t st) {
-    if (g->ewidth == 4) return slot_typed<uint32_t>(g, bs, lanes, out, grid_ctas, st);
-    return slot_typed<unsigned long long>(g, bs, lanes, out, grid_ctas, st);
-}
 
 }  // namespace khop

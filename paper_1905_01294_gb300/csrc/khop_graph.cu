@@ -4,6 +4,8 @@
 #include <new>
 #include <algorithm>
 
+#include <vector>
+
 #include "khop_internal.cuh"
 
 using namespace khop;
@@ -308,6 +310,47 @@ int mark_done(khop_graph *g, cudaStream_t s) {
     return cuda_status(e);
 }
 
+namespace kcache {
+// Per (kernel, device): the dynamic shared memory the kernel was opened to;
+// per (kernel, device, block, smem): its resident CTAs per SM.
+struct KernelAttr { const void *fn; int dev; size_t smem; };
+struct KernelOcc { const void *fn; int dev; int block; size_t smem; int per_sm; };
+static std::mutex g_kmu;
+static std::vector<KernelAttr> g_kattr;
+static std::vector<KernelOcc> g_kocc;
+}  // namespace kcache
+
+int launch_shape(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms, int *grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = -1;
+    {
+        using namespace kcache;
+        std::lock_guard<std::mutex> lk(g_kmu);
+        KernelAttr *at = nullptr;
+        for (KernelAttr &x : g_kattr)
+            if (x.fn == kernel && x.dev == dev) at = &x;
+        if (!at || at->smem < smem) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            if (at) at->smem = smem;
+            else g_kattr.push_back(KernelAttr{kernel, dev, smem});
+        }
+        for (const KernelOcc &x : g_kocc)
+            if (x.fn == kernel && x.dev == dev && x.block == block && x.smem == smem) per_sm = x.per_sm;
+        if (per_sm < 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            g_kocc.push_back(KernelOcc{kernel, dev, block, smem, per_sm});
+        }
+    }
+    if (per_sm <= 0) return KHOP_EINVAL;
+    if (want_per_sm > 0) per_sm = std::min(per_sm, want_per_sm);
+    *grid = per_sm * num_sms;
+    return KHOP_OK;
+}
+
 int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms,
                      int *grid) {
     int per_sm = 0;
@@ -322,7 +365,7 @@ int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm
 void free_batch_state(BatchState &b) {
     cudaFree(b.V);
     for (int i = 0; i < 3; ++i) cudaFree(b.F[i]);
-    for (int i = 0; i < 2; ++i) { cudaFree(b.Q[i]); cudaFree(b.Qpre[i]); cudaFree(b.TF[i]); }
+    for (int i = 0; i < 2; ++i) { cudaFree(b.Q[i]); cudaFree(b.Qpre[i]); cudaFree(b.TF[i]); cudaFree(b.S[i]); }
     cudaFree(b.ctl);
     cudaFree(b.part);
     cudaFree(b.order);
@@ -372,7 +415,7 @@ int alloc_plain_state(khop_graph *g, PlainState &p) {
 
 // Allocate a bit-sliced batch state for graph g (no device sync needed by
 // the caller afterwards).  *bytes receives its size.
-int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw) {
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw, bool sinks) {
     const uint64_t n = g->n;
     const uint64_t before = g->device_bytes;
     b = BatchState{};
@@ -385,6 +428,7 @@ int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw) {
     cudaError_t e = dalloc(g, &b.V, n * lw);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(g, &b.F[i], n * lw);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.Q[i], n);
+    for (int i = 0; i < 2 && e == cudaSuccess && sinks; ++i) e = dalloc(g, &b.S[i], n);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc_raw(g, &b.Qpre[i], n * g->ewidth);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(g, &b.TF[i], g->tf_cap);
     if (e == cudaSuccess) e = dalloc(g, &b.ctl, 1);
@@ -396,6 +440,7 @@ int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw) {
     if (e == cudaSuccess) e = dalloc(g, &b.ch_item, b.ccap);
     if (e == cudaSuccess) e = dalloc_raw(g, &b.ch_start, b.ccap * g->ewidth);
     if (e == cudaSuccess) e = cudaMemset(b.hacc, 0, b.hcap * lw * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b.part, 0, 2 * b.part_rows * 64 * lw * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(b.V, 0, n * lw * sizeof(uint64_t));
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(b.F[i], 0, n * lw * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemset(b.ctl, 0, sizeof(CtlBlock));

@@ -247,7 +247,10 @@ struct RoundSlot {
     unsigned long long scanned;   // in-edges examined by pull
     unsigned long long mf;        // out-edges of the vertices discovered
     unsigned long long unv;       // vertices a pull round had to examine
-    unsigned long long pad[3];
+    unsigned long long defer[2];  // batched pull: deferred in-lists, their chunks
+    unsigned long long seen;      // rolling batch: lanes that discovered a vertex
+    unsigned long long sinks;     // rolling batch: discovered vertices without out-edges
+    unsigned long long pad[7];
 };
 constexpr int kSlotWords = sizeof(RoundSlot) / 8;
 
@@ -283,6 +286,7 @@ struct PlainState {
 // words per vertex in V, F, and the deferred-in-list lane masks).
 struct BatchState {
     uint64_t *V = nullptr;                        // visited lanes per vertex [n]
+    uint32_t *S[2] = {nullptr, nullptr};          // rolling batch: discovered sinks per round [n]
     uint64_t *F[3] = {nullptr, nullptr, nullptr}; // frontier lanes per vertex [n], rotating
     uint32_t *Q[2] = {nullptr, nullptr};          // union-frontier vertices with out-edges
     void *Qpre[2] = {nullptr, nullptr};           // out-edge prefix per queue item (E)
@@ -302,6 +306,34 @@ struct BatchState {
     uint64_t ccap = 0;
     size_t bytes = 0;
     int lw = 1;
+};
+
+// One step of a rolling 64-lane batch (the request server's continuous
+// batching): the host's plan, passed by value as a kernel argument, and the
+// step's outcome, written by the kernel into mapped pinned host memory.
+struct RollPlan {
+    uint32_t nadmit;              // lanes admitted at the start of this step
+    uint32_t reset;               // 1: start from zeroed state (after a step that was given up)
+    unsigned long long act;       // lanes that run this round (admitted lanes included)
+    unsigned long long fin;       // lanes whose k is reached with this round
+    unsigned long long clean;     // retired lanes whose visited marks are still to be cleared
+    uint32_t clean_dense;         // 1: clear them everywhere now (a V sweep)
+    uint32_t pull_ok;             // 0: the round always pushes (see roll_kernel)
+    uint32_t lane[64];            // admission t: lane[t] starts seed[t] (its q_0 = {seed})
+    uint32_t seed[64];
+};
+
+struct RollResult {
+    unsigned long long retired;   // lanes whose count is final after this step
+    unsigned long long cleaned;   // lanes of plan.clean whose visited marks are all gone
+    unsigned long long rdone;     // rounds run by the state so far (after this step)
+    unsigned long long idle;      // 1: no lane continues; every frontier buffer is zero
+    unsigned long long union_nf;  // vertices in the union frontier after the round
+    unsigned long long bytes;     // algorithmic bytes of the round
+    unsigned long long pulled;    // 1 if the round ran as a pull
+    unsigned long long t_start_ns, t_end_ns;   // %globaltimer at the step's start and end (CTA 0)
+    unsigned long long done;      // written last: the step completed
+    unsigned long long count[64]; // the retired lanes' counts
 };
 
 }  // namespace khop
@@ -348,7 +380,8 @@ int cuda_status(cudaError_t e);
 int order_after_previous(khop_graph *g, cudaStream_t s);   // call under g->mu
 int mark_done(khop_graph *g, cudaStream_t s);              // call under g->mu
 int ensure_batch_state(khop_graph *g, int lw = 1);         // call under g->mu
-int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw = 1);  // a standalone state
+// a standalone state; `sinks`: with the rolling batch's sink lists
+int alloc_batch_state(khop_graph *g, BatchState &b, uint64_t *bytes, int lw = 1, bool sinks = false);
 int alloc_plain_state(khop_graph *g, PlainState &p);
 void free_plain_state(PlainState &p);
 void free_batch_state(BatchState &b);
@@ -356,6 +389,11 @@ uint64_t batch_state_bytes(const khop_graph *g);
 uint64_t plain_state_bytes(const khop_graph *g);
 int cooperative_grid(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms,
                      int *grid);
+// Open `kernel` to `smem` bytes of dynamic shared memory (once per device)
+// and give the grid of a cooperative launch (resident CTAs per SM, capped by
+// want_per_sm if > 0, times num_sms); both answers are cached, so a launch
+// path pays for the runtime queries only once.
+int launch_shape(const void *kernel, int block, size_t smem, int want_per_sm, int num_sms, int *grid);
 
 // plain path (khop_plain.cu)
 // keep_visited: every query runs on the grid path, so that after a launch of
@@ -372,10 +410,9 @@ int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, con
 // batched path (khop_batch.cu); lw = 1, 2 or 4 (64, 128 or 256 lanes per traversal)
 int batch_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint64_t nq,
                  uint64_t *out, cudaStream_t st, int lw = 1);
-// One batch of up to 64 lanes on a standalone state.  `lanes` (device,
-// 8-byte aligned) holds seeds[64], ks[64], the lane order[64] (query index or
-// 0xffffffff) and then the 64-bit batch count (1).
-int batch_launch_slot(khop_graph *g, BatchState &bs, const uint32_t *lanes, uint64_t *out,
-                      int grid_ctas, cudaStream_t st);
+// One step of the rolling 64-lane batch held in `bs` (its results go to
+// `res`, device-visible), on at most grid_ctas CTAs.
+int roll_launch(khop_graph *g, BatchState &bs, const RollPlan &plan, RollResult *res,
+                int grid_ctas, cudaStream_t st);
 
 }  // namespace khop

@@ -28,8 +28,10 @@ constexpr uint64_t kPrefetchEdges = 2048;    // next-query seed edges warmed int
 constexpr uint32_t kSoloEdges = 2048;        // 1-hop queries with at most this many seed
                                              // out-edges run on one CTA
 constexpr uint64_t kSoloRun = 8192;          // queries one CTA answers before the grid regroups
-constexpr uint32_t kFuseDeg = 2048;          // seeds with at most this many out-edges get their
-                                             // first two rounds fused into one grid round
+constexpr uint32_t kFuseDeg = 1024;          // seeds with at most this many out-edges get their
+                                             // first two rounds fused into one grid round (every
+                                             // CTA reads the seed row and its heads' offsets, so
+                                             // a larger row makes the prelude L2-bound)
 constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
                                              // vertices are visited) read V before test-and-set
 constexpr int kPullWords = 2;    // bitmap words a warp works on at once in a pull round
@@ -460,15 +462,21 @@ __device__ __forceinline__ uint32_t fused_prelude(const PlainArgs<E> &a, uint32_
     return m1;
 }
 
-// Pull round (masked SpMV over the unvisited vertices).  A warp takes
-// kPullWords 32-vertex bitmap words at once (lane l owns vertex 32 i + l of
-// each), so their loads are in flight together.  Every unvisited vertex first
-// checks its first two in-edges against the frontier bitmap; the in-edges of
-// the vertices still unresolved are then scanned word by word as one
-// flattened list: the warp takes the next 32 * kFlatILP edges of the
+// Pull round (masked SpMV over the unvisited vertices).  Warp w owns the
+// bitmap words w * P + m * S + j (P = kPullWords, S = P * warps of the grid,
+// j < P, m = 0, 1, ...).  It first loads the visited and in-edge-less words
+// of 32 of them at once (one per lane) and keeps only the open words -- those
+// with a vertex that is unvisited and has in-edges -- so closed words cost no
+// dependent round trip (late rounds of a deep query are mostly closed).  The
+// open words are then worked kPullWords at a time (lane l owns vertex 32 i + l
+// of word i), so their loads are in flight together.  Every unvisited vertex
+// first checks its first two in-edges against the frontier bitmap; the
+// in-edges of the vertices still unresolved are then scanned word by word as
+// one flattened list: the warp takes the next 32 * kFlatILP edges of the
 // concatenated remaining in-edge lists (a load-balanced search over the
 // lanes' remaining counts), and a vertex drops out as soon as one of its
-// in-neighbours is in the frontier.
+// in-neighbours is in the frontier.  The output bitmap F_out was zeroed one
+// round ahead, so only words with a discovery are written.
 template <typename E, int BLOCK>
 __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E> &R, Shared &sh,
                                            E *s_winc, E *s_wpos, E *st_pre, E *st_rs, E *st_d) {
@@ -477,108 +485,125 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
     E *wpos = s_wpos + (threadIdx.x >> 5) * 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * BLOCK) >> 5;
+    const uint64_t S = nwarps * kPullWords;                 // stride between a warp's word groups
+    constexpr int kGroups = 32 / kPullWords;                // word groups looked at per batch
+    const uint32_t tail_open = (a.n & 31) ? ~(~0u << (a.n & 31)) : ~0u;   // valid bits of the last word
     uint64_t scanned = 0;
-    for (uint64_t i0 = gwarp * kPullWords; i0 < a.nw; i0 += nwarps * kPullWords) {
-        uint32_t Vw[kPullWords];
-        bool unv[kPullWords], found[kPullWords];
-        E b[kPullWords], e[kPullWords], pos[kPullWords];
-#pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            const uint64_t i = i0 + j;
-            Vw[j] = i < a.nw ? (R.V[i] | a.noin[i]) : ~0u;
-            const uint64_t v = (i << 5) + (uint64_t)lane;
-            unv[j] = i < a.nw && v < a.n && !((Vw[j] >> lane) & 1u);
-            found[j] = false;
+    for (uint64_t c0 = gwarp * kPullWords; c0 < a.nw; c0 += S * kGroups) {
+        // lane l looks at word c0 + (l / P) * S + l % P: closed words are skipped
+        const uint64_t il = c0 + (uint64_t)(lane / kPullWords) * S + (uint64_t)(lane % kPullWords);
+        uint32_t wl = ~0u;
+        if (il < a.nw) {
+            wl = R.V[il] | a.noin[il];
+            if (il == a.nw - 1) wl |= ~tail_open;
         }
+        unsigned open = __ballot_sync(FULL, wl != ~0u);
+        // word looked at by lane L (closed bits of wl include those past n)
+        const auto word_of = [&](int L) {
+            return c0 + (uint64_t)(L / kPullWords) * S + (uint64_t)(L % kPullWords);
+        };
+        while (open) {
+            int Lw[kPullWords];   // lane holding the j-th open word of this step, or -1
+            bool unv[kPullWords], found[kPullWords];
 #pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            b[j] = 0;
-            e[j] = 0;
-            if (unv[j]) {
-                const uint64_t v = ((i0 + j) << 5) + (uint64_t)lane;
-                b[j] = a.cp[v];
-                e[j] = a.cp[v + 1];
+            for (int j = 0; j < kPullWords; ++j) {
+                Lw[j] = open ? __ffs(open) - 1 : -1;
+                open &= open - 1u;
+                const uint32_t w = __shfl_sync(FULL, wl, Lw[j] < 0 ? 0 : Lw[j]);
+                unv[j] = Lw[j] >= 0 && !((w >> lane) & 1u);
+                found[j] = false;
             }
-            pos[j] = b[j];
-        }
-        uint32_t u0[kPullWords], u1[kPullWords];
-        bool l0[kPullWords], l1[kPullWords];
+            E b[kPullWords], e[kPullWords], pos[kPullWords];
 #pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            l0[j] = unv[j] && pos[j] < e[j];
-            l1[j] = l0[j] && pos[j] + 1 < e[j];
-            u0[j] = l0[j] ? a.ri[pos[j]] : 0u;
-            u1[j] = l1[j] ? a.ri[pos[j] + 1] : 0u;
-        }
+            for (int j = 0; j < kPullWords; ++j) {
+                b[j] = 0;
+                e[j] = 0;
+                if (unv[j]) {
+                    const uint64_t v = (word_of(Lw[j]) << 5) + (uint64_t)lane;
+                    b[j] = a.cp[v];
+                    e[j] = a.cp[v + 1];
+                }
+                pos[j] = b[j];
+            }
+            uint32_t u0[kPullWords], u1[kPullWords];
+            bool l0[kPullWords], l1[kPullWords];
 #pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            bool h = l0[j] && ((R.Fin[u0[j] >> 5] >> (u0[j] & 31)) & 1u);
-            h = h || (l1[j] && ((R.Fin[u1[j] >> 5] >> (u1[j] & 31)) & 1u));
-            found[j] = h;
-            pos[j] += (E)l0[j] + (E)l1[j];
-            scanned += (uint64_t)l0[j] + (uint64_t)l1[j];
-        }
+            for (int j = 0; j < kPullWords; ++j) {
+                l0[j] = unv[j] && pos[j] < e[j];
+                l1[j] = l0[j] && pos[j] + 1 < e[j];
+                u0[j] = l0[j] ? a.ri[pos[j]] : 0u;
+                u1[j] = l1[j] ? a.ri[pos[j] + 1] : 0u;
+            }
 #pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            E rem = (unv[j] && !found[j]) ? e[j] - pos[j] : (E)0;
-            while (__any_sync(FULL, rem > 0)) {
-                const E incl = warp_inclusive_sum(rem);
-                const E total = __shfl_sync(FULL, incl, 31);
-                const E excl = incl - rem;
-                winc[lane] = incl;
-                wpos[lane] = pos[j] - excl;   // edge of flat index x owned by lane L: wpos[L] + x
-                __syncwarp();
-                const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
-                uint32_t uu[kFlatILP];
-                int own[kFlatILP];
+            for (int j = 0; j < kPullWords; ++j) {
+                bool h = l0[j] && ((R.Fin[u0[j] >> 5] >> (u0[j] & 31)) & 1u);
+                h = h || (l1[j] && ((R.Fin[u1[j] >> 5] >> (u1[j] & 31)) & 1u));
+                found[j] = h;
+                pos[j] += (E)l0[j] + (E)l1[j];
+                scanned += (uint64_t)l0[j] + (uint64_t)l1[j];
+            }
 #pragma unroll
-                for (int t = 0; t < kFlatILP; ++t) {
-                    const uint32_t x = (uint32_t)(t * 32 + lane);
-                    own[t] = -1;
-                    uu[t] = 0;
-                    if (x < chunk) {
-                        int lo = 0, hi = 31;   // first lane whose inclusive count exceeds x
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
+            for (int j = 0; j < kPullWords; ++j) {
+                E rem = (unv[j] && !found[j]) ? e[j] - pos[j] : (E)0;
+                while (__any_sync(FULL, rem > 0)) {
+                    const E incl = warp_inclusive_sum(rem);
+                    const E total = __shfl_sync(FULL, incl, 31);
+                    const E excl = incl - rem;
+                    winc[lane] = incl;
+                    wpos[lane] = pos[j] - excl;   // edge of flat index x owned by lane L: wpos[L] + x
+                    __syncwarp();
+                    const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
+                    uint32_t uu[kFlatILP];
+                    int own[kFlatILP];
+#pragma unroll
+                    for (int t = 0; t < kFlatILP; ++t) {
+                        const uint32_t x = (uint32_t)(t * 32 + lane);
+                        own[t] = -1;
+                        uu[t] = 0;
+                        if (x < chunk) {
+                            int lo = 0, hi = 31;   // first lane whose inclusive count exceeds x
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
+                            }
+                            own[t] = lo;
+                            uu[t] = a.ri[wpos[lo] + (E)x];
                         }
-                        own[t] = lo;
-                        uu[t] = a.ri[wpos[lo] + (E)x];
                     }
-                }
-                unsigned hits = 0;
+                    unsigned hits = 0;
 #pragma unroll
-                for (int t = 0; t < kFlatILP; ++t)
-                    if (own[t] >= 0 && ((R.Fin[uu[t] >> 5] >> (uu[t] & 31)) & 1u))
-                        hits |= 1u << own[t];
-                hits = __reduce_or_sync(FULL, hits);
-                const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
-                pos[j] += consumed;
-                rem -= consumed;
-                if ((hits >> lane) & 1u) {
-                    found[j] = true;
-                    rem = 0;
+                    for (int t = 0; t < kFlatILP; ++t)
+                        if (own[t] >= 0 && ((R.Fin[uu[t] >> 5] >> (uu[t] & 31)) & 1u))
+                            hits |= 1u << own[t];
+                    hits = __reduce_or_sync(FULL, hits);
+                    const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
+                    pos[j] += consumed;
+                    rem -= consumed;
+                    if ((hits >> lane) & 1u) {
+                        found[j] = true;
+                        rem = 0;
+                    }
+                    if (lane == 0) scanned += chunk;
+                    __syncwarp();
                 }
-                if (lane == 0) scanned += chunk;
-                __syncwarp();
             }
-        }
 #pragma unroll
-        for (int j = 0; j < kPullWords; ++j) {
-            const uint64_t i = i0 + j;
-            if (i >= a.nw) break;
-            const unsigned nm = __ballot_sync(FULL, found[j]);
-            if (lane == 0) {
-                R.Fout[i] = nm;
-                if (nm) atomicOr(&R.V[i], nm);   // V keeps traversal marks only (no in-edge-less bits)
+            for (int j = 0; j < kPullWords; ++j) {
+                if (Lw[j] < 0) break;   // warp-uniform
+                const uint64_t i = word_of(Lw[j]);
+                const unsigned nm = __ballot_sync(FULL, found[j]);
+                if (lane == 0 && nm) {
+                    R.Fout[i] = nm;
+                    atomicOr(&R.V[i], nm);   // V keeps traversal marks only (no in-edge-less bits)
+                }
+                const uint64_t v = (i << 5) + (uint64_t)lane;
+                E rs = 0, d = 0;
+                if (found[j] && !R.last) {
+                    if (a.symmetric) { rs = b[j]; d = e[j] - b[j]; }
+                    else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
+                }
+                record(a, R, found[j], (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
             }
-            const uint64_t v = (i << 5) + (uint64_t)lane;
-            E rs = 0, d = 0;
-            if (found[j] && !R.last) {
-                if (a.symmetric) { rs = b[j]; d = e[j] - b[j]; }
-                else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
-            }
-            record(a, R, found[j], (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
         }
     }
     scanned = warp_sum(scanned);
@@ -796,7 +821,7 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
             a.out[q] = cnt;
             if (a.out_te) a.out_te[q] = deg;
             if (a.stats) {
-                khop_query_stats st{t_prev, now, (uint64_t)deg, 4ull * deg + 2ull * sizeof(E), 1u, 0u};
+                khop_query_stats st{t_prev, now, (uint64_t)deg, 4ull * deg + 2ull * sizeof(E) + 4ull, 1u, 0u};
                 a.stats[q] = st;
             }
             if (a.per_hop) {
@@ -1054,8 +1079,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                         s_nbr[i] = kHashEmpty;
                         s_npos[i] = 0xffffffffu;
                     }
-                bytes += 4ull * mf + 2ull * W * (1ull + m1);
-                bytes += 4ull * mf2 + 2ull * W * (m1 + items_out);
+                bytes += 4ull * mf + (2ull * W + 4ull) + 4ull * m1;                   // round 1
+                bytes += 4ull * mf2 + (2ull * W + 4ull) * m1 + 4ull * items_out;      // round 2
                 te += mf2;
                 sum_mf += mf + mf2;
                 count += m1 + nnew;
@@ -1072,13 +1097,17 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                 r = 2;
                 continue;
             }
+            // Algorithmic bytes: push 4 m_f + (2W + 4) |F| + 4 |F_next| (edge
+            // indices, row offsets and queue entries of the frontier, queue
+            // entries of the next); pull n/8 (visited sweep) + n/8 (next
+            // frontier) + 2W per unvisited vertex with in-edges + 4 per in-edge
+            // scanned.
             if (dir == DIR_PUSH) {
-                bytes += 4ull * mf + 2ull * W * ((r == 1 ? 1ull : items) + items_out);
+                bytes += 4ull * mf + (2ull * W + 4ull) * (r == 1 ? 1ull : items) + 4ull * items_out;
             } else {
                 const uint64_t seen = visited + a.n_noin;
                 const uint64_t unvisited = a.n > seen ? a.n - seen : 0;
-                bytes += 3ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn +
-                         2ull * W * items_out;
+                bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn;
             }
             sum_mf += mf;
             count += nnew;
@@ -1125,13 +1154,11 @@ size_t plain_smem_bytes(uint32_t tile_log2) {
 template <typename E, int BLOCK>
 int launch_block(khop_graph *g, PlainArgs<E> &a, size_t smem, int grid_ctas, cudaStream_t st) {
     const void *fn = (const void *)plain_kernel<E, BLOCK>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
     int grid = 0;
-    int rc = cooperative_grid(fn, BLOCK, smem, g->tune.blocks_per_sm, g->num_sms, &grid);
+    int rc = launch_shape(fn, BLOCK, smem, g->tune.blocks_per_sm, g->num_sms, &grid);
     if (rc != KHOP_OK) return rc;
     if (grid_ctas > 0 && grid_ctas < grid) grid = grid_ctas;
-    e = cudaMemsetAsync(a.ctl, 0, offsetof(CtlBlock, err), st);   // keeps the sticky err
+    cudaError_t e = cudaMemsetAsync(a.ctl, 0, offsetof(CtlBlock, err), st);   // keeps the sticky err
     if (e != cudaSuccess) return cuda_status(e);
     void *args[] = {(void *)&a};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, smem, st);
@@ -1142,7 +1169,8 @@ template <typename E>
 int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                  uint32_t k_all, uint64_t nq, uint64_t *out, uint64_t *out_te,
                  khop_query_stats *stats, uint64_t *per_hop, uint32_t hop_stride, int grid_ctas,
-                 cudaStream_t st, bool keep_visited = false, int32_t *levels = nullptr) {
+                 cudaStream_t st, bool keep_visited = false, int32_t *levels = nullptr,
+                 bool take_test_switch = true) {
     PlainArgs<E> a;
     a.n = g->n;
     a.nnz = g->nnz;
@@ -1189,8 +1217,11 @@ int launch_typed(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uin
                      ? 0ull
                      : std::min<uint64_t>(g->n, (uint64_t)std::ceil((double)g->n / g->tune.beta) + 32);
     a.timeout_ns = g->timeout_ns;
-    a.absent_at = g->absent_at;   // one launch only
-    g->absent_at = 0;
+    a.absent_at = 0;
+    if (take_test_switch) {
+        a.absent_at = g->absent_at;   // one launch only
+        g->absent_at = 0;
+    }
     const size_t smem = plain_smem_bytes<E>(tl);
     switch (g->tune.block_threads) {
         case 256: return launch_block<E, 256>(g, a, smem, grid_ctas, st);
@@ -1214,11 +1245,12 @@ int plain_launch(khop_graph *g, const uint32_t *seeds, const uint32_t *ks, uint3
 
 int plain_launch_state(khop_graph *g, PlainState &ps, const uint32_t *seeds, const uint32_t *ks,
                        uint64_t nq, uint64_t *out, int grid_ctas, cudaStream_t st) {
+    // (a server's launch: the graph's testing switch is left for the graph's own calls)
     if (g->ewidth == 4)
         return launch_typed<uint32_t>(g, ps, seeds, ks, 0, nq, out, nullptr, nullptr, nullptr, 0,
-                                      grid_ctas, st);
+                                      grid_ctas, st, false, nullptr, false);
     return launch_typed<unsigned long long>(g, ps, seeds, ks, 0, nq, out, nullptr, nullptr,
-                                            nullptr, 0, grid_ctas, st);
+                                            nullptr, 0, grid_ctas, st, false, nullptr, false);
 }
 
 }  // namespace khop

@@ -1,17 +1,30 @@
 // Continuous-batching request server for the k-hop count (khop_server_*).
 //
-// Requests (graph, seed, k) arrive from any host thread.  A worker thread
-// keeps them in per-graph FIFO queues by k and runs them in cohorts of up to
-// 64 on bit-sliced batch slots: whenever a slot is free, the oldest waiting
-// request's k picks the cohort, which is filled first with requests of that
-// k and then with requests of smaller k (they finish earlier within the same
-// sweeps), oldest first.  Slots are allocated on demand, each only if free
-// device memory (minus a margin) and the server's budget admit it, up to
-// max_batches per graph; while every slot is busy, requests wait.  Each slot
-// has its own stream and its cohort kernel uses a part of the SMs, so the
-// cohorts of several slots run side by side on the device while the worker
-// admits and completes others.  This is the GPU counterpart of the paper's
-// design that serves many concurrent queries from a thread pool (Sec. II).
+// Requests (graph, seed, k) arrive from any host thread; a worker thread
+// serves them on two kinds of slot, each with its own stream so that the
+// slots' launches run side by side on the device.
+//
+// Heavy requests (k >= 3) are continuously batched at round granularity.  A
+// rolling slot holds one 64-lane bit-sliced traversal on the device and runs
+// it one round per launch (a step, see roll_kernel); lanes are independent,
+// so every step advances each lane in use by one hop whatever its depth.
+// Between steps the worker posts the result of every lane the step retired
+// (its k-th round ran, or its frontier came out empty) the moment the step
+// completes, and admits waiting requests into the free lanes, each with its
+// own round counter: a request that arrives while a traversal runs joins it
+// at the next round boundary.  A retired lane is reused once its marks are
+// gone (see roll_kernel); when lanes run short the worker asks a step for a
+// clearing sweep.  Deep traversals share their large middle rounds this way,
+// so heavy slots are few (at most two per graph, max_batches permitting).
+//
+// Light requests (k <= 2) cost a few microseconds each on the single-query
+// kernel, less than one round of a batch, so plain slots answer them in
+// arrival order, up to kPlainBatch per persistent launch.
+//
+// Slots are allocated on demand, each only if free device memory (minus a
+// margin) and the server's budget admit its state.  This is the GPU
+// counterpart of the paper's thread pool serving many concurrent queries at
+// low latency (Sec. II).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -30,8 +43,14 @@ namespace {
 
 using namespace khop;
 
-constexpr int kLaneWords = 64 * 3 + 2;   // seeds, ks, order, then the batch count (u64)
 constexpr uint64_t kMarginBytes = 1ull << 30;
+constexpr int kLanes = 64;
+constexpr size_t kHeavySlots = 2;    // rolling slots per graph at most
+constexpr size_t kPlainSlots = 2;    // plain slots per graph at most
+constexpr int kPlainBatch = 16;      // light requests per plain launch at most
+constexpr uint32_t kAdmitWindow = 1; // default: a rolling slot admits while its lanes have run <= 1 round
+constexpr int32_t kPlainHeavy = 2;   // default: heavy requests also take the single-query path while at
+                                     // most this many wait (a traversal alone beats a batch's launches)
 
 uint64_t now_ns() {
     timespec ts;
@@ -46,28 +65,55 @@ struct Request {
     uint64_t t_submit;
 };
 
-constexpr size_t kPlainCohort = 2;   // cohorts this small run on the plain kernel
+bool light(uint32_t k) { return k <= 2; }
 
+struct Lane {
+    bool used = false;     // holds a request
+    bool dirty = false;    // retired, its visited marks not yet cleared (not reusable)
+    bool fwait = false;    // retired, its bits still in the next frontier buffer (not reusable)
+    uint64_t ret_round = 0;   // the state's round count when it retired
+    Request req{};
+    uint32_t rounds = 0;   // rounds completed
+};
+
+bool lane_free(const Lane &ln) { return !ln.used && !ln.dirty && !ln.fwait; }
+
+// A rolling 64-lane batch.
 struct Slot {
     BatchState st;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    RollResult *h_res = nullptr;   // mapped pinned memory, written by the step kernel
+    RollResult *d_res = nullptr;   // its device address
+    Lane lane[kLanes];
+    int used = 0;                  // lanes in use
+    int ndirty = 0;                // lanes waiting to be cleaned
+    bool busy = false;             // a step is in flight
+    bool lost = false;             // that step was given up: its requests already failed
+    bool reset = false;            // the next step starts from zeroed state
+    uint64_t t_launch = 0;
+    std::vector<std::pair<uint32_t, uint32_t>> admit;   // (lane, seed) for the next step
+};
+
+// Single-query path: one persistent launch answers a list of light requests.
+struct PlainSlot {
     PlainState pst;
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    uint32_t *d_lanes = nullptr;
-    uint64_t *d_out = nullptr;
-    uint32_t *h_lanes = nullptr;   // pinned
-    uint64_t *h_out = nullptr;     // pinned
-    std::vector<Request> reqs;     // the cohort in flight
-    bool busy = false;
-    bool timed_out = false;
+    cudaEvent_t ev = nullptr;
+    uint32_t *d_q = nullptr, *h_q = nullptr;   // seeds[kPlainBatch], ks[kPlainBatch] (h_q pinned)
+    uint64_t *h_out = nullptr, *d_out = nullptr;   // counts: mapped pinned memory the kernel writes
+    std::vector<Request> reqs;     // the launch in flight
+    bool busy = false, lost = false;
     uint64_t t_launch = 0;
 };
 
 struct GraphCtx {
     khop_graph *g = nullptr;
-    std::deque<Request> pending[64];   // by min(k, 63)
-    uint64_t npending = 0;
+    std::deque<Request> pending[2];   // light, heavy
     std::vector<Slot *> slots;
+    std::vector<PlainSlot *> pslots;
+    bool alloc_failed = false;       // the last rolling-slot allocation was refused
+    bool palloc_failed = false;      // the last plain-slot allocation was refused
 };
 
 }  // namespace
@@ -81,10 +127,14 @@ struct khop_server {
     std::deque<Request> inbox;
     std::deque<khop_result> outbox;
     bool stop = false;
+    std::atomic<int64_t> timeout_us{2000000};
+    uint32_t admit_rounds = kAdmitWindow;
+    int32_t plain_heavy = kPlainHeavy;
     uint64_t next_ticket = 1;
-    uint64_t submitted = 0, completed = 0, steps = 0, slots_allocated = 0;
+    khop_server_counters c{};
     uint64_t queued = 0;            // submitted and not yet completed
     uint64_t mem_used = 0;          // device bytes of the slots
+    uint64_t lanes_busy = 0;        // worker-owned
     std::map<khop_graph *, GraphCtx *> graphs;   // worker-owned
     std::thread worker;
 };
@@ -101,34 +151,46 @@ void post(khop_server *s, const Request &r, uint64_t count, int status) {
     res.t_done_ns = now_ns();
     std::lock_guard<std::mutex> lk(s->mu);
     s->outbox.push_back(res);
-    s->completed++;
+    s->c.completed++;
+    if (status == KHOP_ETIMEDOUT) s->c.timed_out++;
     s->queued--;
     s->cv_out.notify_all();
 }
 
-void free_slot(khop_server *s, Slot *sl) {
-    if (sl->stream) cudaStreamSynchronize(sl->stream);
-    free_batch_state(sl->st);
-    free_plain_state(sl->pst);
-    cudaFree(sl->d_lanes);
-    cudaFree(sl->d_out);
-    cudaFreeHost(sl->h_lanes);
-    cudaFreeHost(sl->h_out);
-    if (sl->done) cudaEventDestroy(sl->done);
-    if (sl->stream) cudaStreamDestroy(sl->stream);
-    delete sl;
-    (void)s;
+bool admit_memory(khop_server *s, uint64_t need) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
+    if ((uint64_t)fr < need + kMarginBytes) return false;
+    return !(s->opts.mem_budget_bytes && s->mem_used + need > s->opts.mem_budget_bytes);
 }
 
-// A new slot for ctx if memory and the budget admit it, else null.
+void free_slot(Slot *sl) {
+    if (sl->stream) cudaStreamSynchronize(sl->stream);
+    free_batch_state(sl->st);
+    if (sl->h_res) cudaFreeHost(sl->h_res);
+    if (sl->ev) cudaEventDestroy(sl->ev);
+    if (sl->stream) cudaStreamDestroy(sl->stream);
+    delete sl;
+}
+
+void free_pslot(PlainSlot *ps) {
+    if (ps->stream) cudaStreamSynchronize(ps->stream);
+    free_plain_state(ps->pst);
+    cudaFree(ps->d_q);
+    cudaFreeHost(ps->h_q);
+    if (ps->h_out) cudaFreeHost(ps->h_out);
+    if (ps->ev) cudaEventDestroy(ps->ev);
+    if (ps->stream) cudaStreamDestroy(ps->stream);
+    delete ps;
+}
+
+// A new rolling slot for ctx if the cap, memory and the budget admit it.
 Slot *try_alloc_slot(khop_server *s, GraphCtx *ctx) {
-    const uint64_t cap = s->opts.max_batches ? s->opts.max_batches : 8;
+    const uint64_t cap = std::min<uint64_t>(s->opts.max_batches ? s->opts.max_batches : kHeavySlots,
+                                            kHeavySlots);
     if (ctx->slots.size() >= cap) return nullptr;
-    const uint64_t need = batch_state_bytes(ctx->g) + plain_state_bytes(ctx->g) + 4096;
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return nullptr;
-    if ((uint64_t)fr < need + kMarginBytes) return nullptr;
-    if (s->opts.mem_budget_bytes && s->mem_used + need > s->opts.mem_budget_bytes) return nullptr;
+    const uint64_t need = batch_state_bytes(ctx->g) + 2 * ctx->g->n * sizeof(uint32_t) + 4096;   // + sink lists
+    if (!admit_memory(s, need)) return nullptr;
     Slot *sl = new (std::nothrow) Slot();
     if (!sl) return nullptr;
     uint64_t bytes = 0;
@@ -136,103 +198,245 @@ Slot *try_alloc_slot(khop_server *s, GraphCtx *ctx) {
     {
         // the slot belongs to the server, not to the graph's own accounting
         std::lock_guard<std::mutex> glk(ctx->g->mu);
-        ok = alloc_batch_state(ctx->g, sl->st, &bytes) == KHOP_OK;
+        ok = alloc_batch_state(ctx->g, sl->st, &bytes, 1, true) == KHOP_OK;
         if (ok) ctx->g->device_bytes -= bytes;
-        ok = ok && alloc_plain_state(ctx->g, sl->pst) == KHOP_OK;
-        if (ok) {
-            ctx->g->device_bytes -= sl->pst.bytes;
-            bytes += sl->pst.bytes;
-        }
     }
     ok = ok && cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaMalloc(&sl->d_lanes, kLaneWords * sizeof(uint32_t)) == cudaSuccess;
-    ok = ok && cudaMalloc(&sl->d_out, 64 * sizeof(uint64_t)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&sl->h_lanes, kLaneWords * sizeof(uint32_t)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&sl->h_out, 64 * sizeof(uint64_t)) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&sl->h_res, sizeof(RollResult), cudaHostAllocMapped) == cudaSuccess;
+    ok = ok && cudaHostGetDevicePointer((void **)&sl->d_res, sl->h_res, 0) == cudaSuccess;
     if (!ok) {
-        free_slot(s, sl);
+        free_slot(sl);
         return nullptr;
     }
-    s->mem_used += bytes + kLaneWords * 4 + 64 * 8;
+    memset(sl->h_res, 0, sizeof(RollResult));
+    s->mem_used += bytes;
     ctx->slots.push_back(sl);
     std::lock_guard<std::mutex> lk(s->mu);
-    s->slots_allocated++;
+    s->c.slots_allocated++;
     return sl;
 }
 
-// Take the next cohort of ctx: the oldest request's k, then smaller k.
-void take_cohort(GraphCtx *ctx, std::vector<Request> &out) {
-    int kb = -1;
-    uint64_t oldest = ~0ull;
-    for (int b = 1; b < 64; ++b)
-        if (!ctx->pending[b].empty() && ctx->pending[b].front().t_submit < oldest) {
-            oldest = ctx->pending[b].front().t_submit;
-            kb = b;
-        }
-    out.clear();
-    for (int b = kb; b >= 1 && out.size() < 64; --b) {
-        auto &q = ctx->pending[b];
-        while (!q.empty() && out.size() < 64) {
-            out.push_back(q.front());
-            q.pop_front();
-        }
+// A new plain slot for ctx if the cap, memory and the budget admit it.
+PlainSlot *try_alloc_pslot(khop_server *s, GraphCtx *ctx) {
+    if (ctx->pslots.size() >= kPlainSlots) return nullptr;
+    const uint64_t need = plain_state_bytes(ctx->g) + 4096;
+    if (!admit_memory(s, need)) return nullptr;
+    PlainSlot *ps = new (std::nothrow) PlainSlot();
+    if (!ps) return nullptr;
+    bool ok;
+    {
+        std::lock_guard<std::mutex> glk(ctx->g->mu);
+        ok = alloc_plain_state(ctx->g, ps->pst) == KHOP_OK;
+        if (ok) ctx->g->device_bytes -= ps->pst.bytes;
     }
-    ctx->npending -= out.size();
+    ok = ok && cudaStreamCreateWithFlags(&ps->stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ps->ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&ps->d_q, 2 * kPlainBatch * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ps->h_q, 2 * kPlainBatch * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void **)&ps->h_out, kPlainBatch * sizeof(uint64_t), cudaHostAllocMapped) ==
+                   cudaSuccess;
+    ok = ok && cudaHostGetDevicePointer((void **)&ps->d_out, ps->h_out, 0) == cudaSuccess;
+    if (!ok) {
+        free_pslot(ps);
+        return nullptr;
+    }
+    s->mem_used += ps->pst.bytes;
+    ctx->pslots.push_back(ps);
+    return ps;
 }
 
-int launch_cohort(khop_server *s, GraphCtx *ctx, Slot *sl) {
-    take_cohort(ctx, sl->reqs);
-    const size_t c = sl->reqs.size();
-    for (int l = 0; l < 64; ++l) {
-        const bool on = (size_t)l < c;
-        sl->h_lanes[l] = on ? sl->reqs[l].seed : 0u;
-        sl->h_lanes[64 + l] = on ? sl->reqs[l].k : 0u;
-        sl->h_lanes[128 + l] = on ? (uint32_t)l : 0xffffffffu;
+// Fail every request holding a lane of sl and free the lanes; the slot
+// restarts from zeroed state.
+void fail_lanes(khop_server *s, Slot *sl, int status) {
+    for (Lane &ln : sl->lane)
+        if (ln.used) {
+            post(s, ln.req, ~0ull, status);
+            ln.used = false;
+        }
+    for (Lane &ln : sl->lane) ln.dirty = ln.fwait = false;
+    sl->ndirty = 0;
+    s->lanes_busy -= (uint64_t)sl->used;
+    sl->used = 0;
+    sl->admit.clear();
+    sl->reset = true;
+}
+
+int free_lanes(const Slot *sl) {
+    int c = 0;
+    for (const Lane &ln : sl->lane) c += lane_free(ln);
+    return c;
+}
+
+// Take waiting heavy requests of ctx into the free lanes of sl, oldest first,
+// while the slot's traversal is in its admission window: a pull round skips
+// a vertex's remaining in-edges only once every lane that needs the vertex
+// found a parent, which lanes with small frontiers (just admitted) rarely
+// do, so a traversal whose lanes went deep takes no new lanes until it drains.
+void admit(khop_server *s, GraphCtx *ctx, Slot *sl) {
+    int nfree = free_lanes(sl);
+    std::deque<Request> &q = ctx->pending[1];
+    if (nfree == 0 || q.empty()) return;
+    for (const Lane &ln : sl->lane)
+        if (ln.used && ln.rounds > s->admit_rounds) return;
+    const bool running = sl->used > 0;
+    int l = 0;
+    uint64_t joined = 0;
+    while (!q.empty() && nfree > 0) {
+        while (!lane_free(sl->lane[l])) ++l;
+        --nfree;
+        Lane &ln = sl->lane[l];
+        ln.used = true;
+        ln.req = q.front();
+        ln.rounds = 0;
+        q.pop_front();
+        sl->admit.emplace_back((uint32_t)l, ln.req.seed);
+        sl->used++;
+        s->lanes_busy++;
+        joined += running;
     }
-    const unsigned long long one = 1ull;
-    memcpy(sl->h_lanes + 192, &one, sizeof(one));
-    cudaError_t e = cudaMemcpyAsync(sl->d_lanes, sl->h_lanes, kLaneWords * sizeof(uint32_t),
-                                    cudaMemcpyHostToDevice, sl->stream);
-    int rc = cuda_status(e);
-    if (rc == KHOP_OK) {
-        if (c <= kPlainCohort)   // one or two queries: the single-query kernel is cheaper
-            rc = plain_launch_state(ctx->g, sl->pst, sl->d_lanes, sl->d_lanes + 64, c, sl->d_out,
-                                    s->grid_ctas, sl->stream);
-        else
-            rc = batch_launch_slot(ctx->g, sl->st, sl->d_lanes, sl->d_out, s->grid_ctas, sl->stream);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->c.joined_running += joined;
+    if (s->lanes_busy > s->c.max_lanes_busy) s->c.max_lanes_busy = s->lanes_busy;
+}
+
+// Launch the next step of sl: one round for every lane in use.
+void launch_step(khop_server *s, GraphCtx *ctx, Slot *sl) {
+    RollPlan p{};
+    p.nadmit = (uint32_t)sl->admit.size();
+    for (size_t t = 0; t < sl->admit.size(); ++t) {
+        p.lane[t] = sl->admit[t].first;
+        p.seed[t] = sl->admit[t].second;
     }
-    if (rc == KHOP_OK)
-        rc = cuda_status(cudaMemcpyAsync(sl->h_out, sl->d_out, 64 * sizeof(uint64_t),
-                                         cudaMemcpyDeviceToHost, sl->stream));
-    if (rc == KHOP_OK) rc = cuda_status(cudaEventRecord(sl->done, sl->stream));
+    sl->admit.clear();
+    for (int l = 0; l < kLanes; ++l) {
+        const Lane &ln = sl->lane[l];
+        if (ln.dirty) p.clean |= 1ull << l;
+        if (!ln.used) continue;
+        p.act |= 1ull << l;
+        if ((uint64_t)ln.rounds + 1 >= (uint64_t)ln.req.k) p.fin |= 1ull << l;
+    }
+    // lanes run short while requests wait: clear the retired lanes' marks now
+    p.clean_dense = (p.clean != 0ull && !ctx->pending[1].empty() && free_lanes(sl) <= kLanes / 2) ? 1u : 0u;
+    p.pull_ok = 1u;   // lanes of a slot are within kAdmitWindow + 1 rounds of each other
+    p.reset = sl->reset ? 1u : 0u;
+    sl->reset = false;
+    sl->h_res->done = 0ull;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->c.clean_steps += p.clean_dense;
+        s->c.lane_steps += (uint64_t)__builtin_popcountll(p.act);
+    }
+    int rc = roll_launch(ctx->g, sl->st, p, sl->d_res, s->grid_ctas, sl->stream);
+    if (rc == KHOP_OK) rc = cuda_status(cudaEventRecord(sl->ev, sl->stream));
     if (rc != KHOP_OK) {
-        for (auto &r : sl->reqs) post(s, r, ~0ull, rc);
-        sl->reqs.clear();
-        return rc;
+        fail_lanes(s, sl, rc);
+        return;
     }
     sl->busy = true;
-    sl->timed_out = false;
+    sl->lost = false;
     sl->t_launch = now_ns();
     std::lock_guard<std::mutex> lk(s->mu);
-    s->steps++;
-    return KHOP_OK;
+    s->c.steps++;
 }
 
-void finish_slot(khop_server *s, Slot *sl, int status) {
-    if (!sl->timed_out)
-        for (size_t i = 0; i < sl->reqs.size(); ++i)
-            post(s, sl->reqs[i], status == KHOP_OK ? sl->h_out[i] : ~0ull, status);
-    sl->reqs.clear();
+// A step of sl completed: post the retired lanes, advance the others.
+void finish_step(khop_server *s, Slot *sl) {
     sl->busy = false;
-    sl->timed_out = false;
+    if (sl->lost) {   // its requests failed already; the device state is abandoned
+        sl->lost = false;
+        for (Lane &ln : sl->lane) ln.used = ln.dirty = ln.fwait = false;
+        sl->ndirty = 0;
+        s->lanes_busy -= (uint64_t)sl->used;
+        sl->used = 0;
+        sl->reset = true;
+        return;
+    }
+    const RollResult &r = *sl->h_res;
+    if (r.done != 1ull) {
+        fail_lanes(s, sl, KHOP_EDEVICE);
+        return;
+    }
+    const unsigned long long retired = r.retired;
+    uint64_t early = 0;
+    for (int l = 0; l < kLanes; ++l) {
+        Lane &ln = sl->lane[l];
+        if (ln.dirty && ((r.cleaned >> l) & 1ull)) {
+            ln.dirty = false;
+            sl->ndirty--;
+        }
+        // stale frontier bits are gone once the buffer holding them was
+        // consumed by a later round, or the state emptied
+        if (ln.fwait && (r.idle || r.rdone > ln.ret_round)) ln.fwait = false;
+        if (!ln.used) continue;
+        if ((retired >> l) & 1ull) {
+            if ((uint64_t)ln.rounds + 1 < (uint64_t)ln.req.k) ++early;
+            post(s, ln.req, r.count[l], KHOP_OK);
+            ln.used = false;
+            if (r.count[l] != 0ull) {
+                // it marked vertices besides its seed (whose mark is cleared already),
+                // and its last discoveries are in the next frontier buffer
+                ln.dirty = true;
+                sl->ndirty++;
+                ln.fwait = r.idle == 0ull;
+                ln.ret_round = r.rdone;
+            }
+            sl->used--;
+            s->lanes_busy--;
+        } else {
+            ln.rounds++;
+        }
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->c.retired_early += early;
+    s->c.gpu_step_ns += r.t_end_ns > r.t_start_ns ? r.t_end_ns - r.t_start_ns : 0ull;
+    s->c.pull_steps += r.pulled;
+}
+
+// Launch the oldest waiting requests of queue `cls` of ctx on the plain slot ps.
+void launch_plain(khop_server *s, GraphCtx *ctx, PlainSlot *ps, int cls) {
+    std::deque<Request> &q = ctx->pending[cls];
+    ps->reqs.clear();
+    while (!q.empty() && (int)ps->reqs.size() < kPlainBatch) {
+        ps->reqs.push_back(q.front());
+        q.pop_front();
+    }
+    const size_t c = ps->reqs.size();
+    for (size_t i = 0; i < c; ++i) {
+        ps->h_q[i] = ps->reqs[i].seed;
+        ps->h_q[kPlainBatch + i] = ps->reqs[i].k;
+    }
+    int rc = cuda_status(cudaMemcpyAsync(ps->d_q, ps->h_q, 2 * kPlainBatch * sizeof(uint32_t),
+                                         cudaMemcpyHostToDevice, ps->stream));
+    if (rc == KHOP_OK)
+        rc = plain_launch_state(ctx->g, ps->pst, ps->d_q, ps->d_q + kPlainBatch, c, ps->d_out, s->grid_ctas,
+                                ps->stream);   // (s->grid_ctas: half the SMs' CTA slots, see create)
+    if (rc == KHOP_OK) rc = cuda_status(cudaEventRecord(ps->ev, ps->stream));
+    if (rc != KHOP_OK) {
+        for (const Request &r : ps->reqs) post(s, r, ~0ull, rc);
+        ps->reqs.clear();
+        return;
+    }
+    ps->busy = true;
+    ps->lost = false;
+    ps->t_launch = now_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->c.plain_launches++;
+}
+
+void finish_plain(khop_server *s, PlainSlot *ps, int status) {
+    ps->busy = false;
+    if (!ps->lost)
+        for (size_t i = 0; i < ps->reqs.size(); ++i)
+            post(s, ps->reqs[i], status == KHOP_OK ? ps->h_out[i] : ~0ull, status);
+    ps->reqs.clear();
+    ps->lost = false;
 }
 
 void worker_main(khop_server *s) {
     cudaSetDevice(s->device);
-    const uint64_t timeout_ns =
-        (uint64_t)(s->opts.wait_timeout_us > 0 ? s->opts.wait_timeout_us : 2000000) * 1000ull;
     std::vector<Request> incoming;
+    uint64_t t_active = now_ns();   // the last time the worker had something to do
     for (;;) {
         bool stopping;
         {
@@ -247,80 +451,152 @@ void worker_main(khop_server *s) {
                 ctx = new GraphCtx();
                 ctx->g = r.g;
             }
-            ctx->pending[std::min<uint32_t>(r.k, 63)].push_back(r);
-            ctx->npending++;
+            ctx->pending[light(r.k) ? 0 : 1].push_back(r);
         }
         incoming.clear();
+        const uint64_t timeout_ns = (uint64_t)s->timeout_us.load() * 1000ull;
         // completions
         bool busy = false;
-        for (auto &kv : s->graphs)
+        for (auto &kv : s->graphs) {
             for (Slot *sl : kv.second->slots) {
                 if (!sl->busy) continue;
-                const cudaError_t q = cudaEventQuery(sl->done);
+                const cudaError_t q = cudaEventQuery(sl->ev);
                 if (q == cudaSuccess) {
-                    finish_slot(s, sl, KHOP_OK);
+                    finish_step(s, sl);
                 } else if (q == cudaErrorNotReady) {
                     busy = true;
-                    if (!sl->timed_out && now_ns() - sl->t_launch > timeout_ns) {
-                        for (auto &r : sl->reqs) post(s, r, ~0ull, KHOP_ETIMEDOUT);
-                        sl->timed_out = true;   // the slot stays reserved until it completes
+                    if (!sl->lost && now_ns() - sl->t_launch > timeout_ns) {
+                        // give the step up: its requests fail now; the slot is
+                        // reused (from zeroed state) once the step completes
+                        fail_lanes(s, sl, KHOP_ETIMEDOUT);
+                        sl->lost = true;
                     }
                 } else {
-                    finish_slot(s, sl, KHOP_ECUDA);
+                    fail_lanes(s, sl, KHOP_ECUDA);
+                    sl->busy = false;
                 }
             }
-        if (stopping) {
-            if (busy) {
-                for (auto &kv : s->graphs)
-                    for (Slot *sl : kv.second->slots)
-                        if (sl->busy) {
-                            const cudaError_t e = cudaStreamSynchronize(sl->stream);
-                            finish_slot(s, sl, e == cudaSuccess ? KHOP_OK : KHOP_ECUDA);
-                        }
+            for (PlainSlot *ps : kv.second->pslots) {
+                if (!ps->busy) continue;
+                const cudaError_t q = cudaEventQuery(ps->ev);
+                if (q == cudaSuccess) {
+                    finish_plain(s, ps, KHOP_OK);
+                } else if (q == cudaErrorNotReady) {
+                    busy = true;
+                    if (!ps->lost && now_ns() - ps->t_launch > timeout_ns) {
+                        for (const Request &r : ps->reqs) post(s, r, ~0ull, KHOP_ETIMEDOUT);
+                        ps->lost = true;   // reused once the launch completes
+                    }
+                } else {
+                    finish_plain(s, ps, KHOP_ECUDA);
+                }
             }
+        }
+        if (stopping) {
             for (auto &kv : s->graphs) {
                 GraphCtx *ctx = kv.second;
-                for (int b = 0; b < 64; ++b)
-                    for (auto &r : ctx->pending[b]) post(s, r, ~0ull, KHOP_ESHUTDOWN);
-                for (Slot *sl : ctx->slots) free_slot(s, sl);
+                // launches are bounded (every device wait is); what they do not
+                // finish fails below
+                for (Slot *sl : ctx->slots)
+                    if (sl->busy) {
+                        cudaStreamSynchronize(sl->stream);
+                        finish_step(s, sl);
+                    }
+                for (PlainSlot *ps : ctx->pslots)
+                    if (ps->busy) {
+                        const cudaError_t e = cudaStreamSynchronize(ps->stream);
+                        finish_plain(s, ps, e == cudaSuccess ? KHOP_OK : KHOP_ECUDA);
+                    }
+                for (Slot *sl : ctx->slots) {
+                    fail_lanes(s, sl, KHOP_ESHUTDOWN);
+                    free_slot(sl);
+                }
+                for (PlainSlot *ps : ctx->pslots) free_pslot(ps);
+                for (auto &q : ctx->pending)
+                    for (auto &r : q) post(s, r, ~0ull, KHOP_ESHUTDOWN);
                 delete ctx;
             }
             s->graphs.clear();
             return;
         }
-        // admissions: fill every free (or newly admitted) slot
-        bool launched = false, pending = false;
+        // launches: every idle plain slot takes the oldest light requests;
+        // every rolling slot at a step boundary admits heavy requests into its
+        // free lanes and runs its next step; requests left over get new slots
+        // while the caps, memory and the budget allow
+        bool launched = false;
         for (auto &kv : s->graphs) {
             GraphCtx *ctx = kv.second;
-            while (ctx->npending) {
-                Slot *free_sl = nullptr;
-                for (Slot *sl : ctx->slots)
-                    if (!sl->busy) { free_sl = sl; break; }
-                if (!free_sl) free_sl = try_alloc_slot(s, ctx);
-                if (!free_sl) {
-                    if (ctx->slots.empty()) {
-                        // no slot could ever run these: fail them
-                        for (int b = 0; b < 64; ++b) {
-                            for (auto &r : ctx->pending[b]) post(s, r, ~0ull, KHOP_ENOMEM);
-                            ctx->pending[b].clear();
-                        }
-                        ctx->npending = 0;
-                    }
+            // light requests first; heavy ones too while only a few wait
+            const auto plain_cls = [&]() {
+                if (!ctx->pending[0].empty()) return 0;
+                if (!ctx->pending[1].empty() && s->plain_heavy >= 0 &&
+                    ctx->pending[1].size() <= (size_t)s->plain_heavy)
+                    return 1;
+                return -1;
+            };
+            for (PlainSlot *ps : ctx->pslots) {
+                const int c = plain_cls();
+                if (c < 0) break;
+                if (!ps->busy) {
+                    launch_plain(s, ctx, ps, c);
+                    launched = true;
+                }
+            }
+            while (plain_cls() >= 0 && !ctx->palloc_failed) {
+                PlainSlot *ps = try_alloc_pslot(s, ctx);
+                if (!ps) {
+                    ctx->palloc_failed = true;
                     break;
                 }
-                launch_cohort(s, ctx, free_sl);
+                launch_plain(s, ctx, ps, plain_cls());
                 launched = true;
             }
-            if (ctx->npending) pending = true;
+            for (Slot *sl : ctx->slots) {
+                if (sl->busy) continue;
+                admit(s, ctx, sl);
+                // all of its lanes wait for cleaning while requests wait: a
+                // step that only clears their marks
+                const bool need_clean = sl->ndirty > 0 && sl->used == 0 && free_lanes(sl) <= kLanes / 2 &&
+                                        !ctx->pending[1].empty();
+                if (sl->used > 0 || need_clean) {
+                    launch_step(s, ctx, sl);
+                    launched = true;
+                }
+            }
+            while (!ctx->pending[1].empty() && !ctx->alloc_failed) {
+                Slot *sl = try_alloc_slot(s, ctx);
+                if (!sl) {
+                    ctx->alloc_failed = true;
+                    break;
+                }
+                admit(s, ctx, sl);
+                launch_step(s, ctx, sl);
+                launched = true;
+            }
+            // requests that no slot of their kind could ever run fail
+            if (ctx->pslots.empty() && ctx->palloc_failed) {
+                for (auto &r : ctx->pending[0]) post(s, r, ~0ull, KHOP_ENOMEM);
+                ctx->pending[0].clear();
+            }
+            if (ctx->slots.empty() && ctx->alloc_failed) {
+                for (auto &r : ctx->pending[1]) post(s, r, ~0ull, KHOP_ENOMEM);
+                ctx->pending[1].clear();
+            }
+            if (ctx->pending[0].empty()) ctx->palloc_failed = false;   // try again next time
+            if (ctx->pending[1].empty()) ctx->alloc_failed = false;
         }
+        // poll again at once while launches run or requests came lately: a
+        // timed sleep or a condition-variable wake-up here costs tens of
+        // microseconds, longer than a light request's whole launch
+        const uint64_t now = now_ns();
+        if (launched || busy) t_active = now;
         if (launched) continue;
-        if (busy) {
-            std::this_thread::sleep_for(std::chrono::microseconds(2));
+        if (busy || now - t_active < 200000ull) {
+            std::this_thread::yield();
             continue;
         }
         std::unique_lock<std::mutex> lk(s->mu);
-        if (s->inbox.empty() && !s->stop)
-            s->cv_in.wait_for(lk, std::chrono::milliseconds(pending ? 1 : 50));
+        if (s->inbox.empty() && !s->stop) s->cv_in.wait_for(lk, std::chrono::milliseconds(50));
     }
 }
 
@@ -331,10 +607,14 @@ extern "C" {
 int khop_server_create(const khop_server_opts *opts, khop_server **out) {
     if (!out) return KHOP_EINVAL;
     *out = nullptr;
+    if (opts && opts->wait_timeout_us < 0) return KHOP_EINVAL;
     khop_server *s = new (std::nothrow) khop_server();
     if (!s) return KHOP_ENOMEM;
     if (opts) s->opts = *opts;
     if (s->opts.max_pending == 0) s->opts.max_pending = 1u << 20;
+    s->timeout_us = s->opts.wait_timeout_us > 0 ? s->opts.wait_timeout_us : 2000000;
+    s->admit_rounds = s->opts.admit_rounds ? s->opts.admit_rounds : kAdmitWindow;
+    s->plain_heavy = s->opts.plain_heavy ? s->opts.plain_heavy : kPlainHeavy;
     int nsm = 0;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
@@ -342,7 +622,10 @@ int khop_server_create(const khop_server_opts *opts, khop_server **out) {
         delete s;
         return cuda_status(e);
     }
-    s->grid_ctas = nsm;   // one CTA per SM: two cohort kernels fit side by side
+    // every launch of the server (steps, plain launches) on half the SMs'
+    // worth of CTAs: four of them are resident at once (two per SM), so a
+    // light request's launch never waits for a traversal's step to end
+    s->grid_ctas = std::max(1, nsm / 2);
     try {
         s->worker = std::thread(worker_main, s);
     } catch (...) {
@@ -350,6 +633,12 @@ int khop_server_create(const khop_server_opts *opts, khop_server **out) {
         return KHOP_ENOMEM;
     }
     *out = s;
+    return KHOP_OK;
+}
+
+int khop_server_set_wait_timeout(khop_server *s, int64_t wait_timeout_us) {
+    if (!s || wait_timeout_us < 0) return KHOP_EINVAL;
+    s->timeout_us = wait_timeout_us > 0 ? wait_timeout_us : 2000000;
     return KHOP_OK;
 }
 
@@ -361,13 +650,13 @@ int khop_submit(khop_server *s, khop_graph *g, uint32_t seed, uint32_t k, uint64
     if (s->queued >= s->opts.max_pending) return KHOP_EBUSY;
     Request r{s->next_ticket++, g, seed, k, now_ns()};
     *ticket = r.ticket;
-    s->submitted++;
+    s->c.submitted++;
     s->queued++;
     if (k == 0) {
         // nothing to traverse: complete at once
         khop_result res{r.ticket, 0ull, KHOP_OK, k, r.t_submit, now_ns()};
         s->outbox.push_back(res);
-        s->completed++;
+        s->c.completed++;
         s->queued--;
         s->cv_out.notify_all();
         return KHOP_OK;
@@ -390,12 +679,12 @@ int khop_submit_many(khop_server *s, khop_graph *g, const uint32_t *seeds, const
     for (uint32_t i = 0; i < count; ++i) {
         Request r{s->next_ticket++, g, seeds[i], ks[i], t};
         tickets[i] = r.ticket;
-        s->submitted++;
+        s->c.submitted++;
         s->queued++;
         if (ks[i] == 0) {
             khop_result res{r.ticket, 0ull, KHOP_OK, 0u, t, now_ns()};
             s->outbox.push_back(res);
-            s->completed++;
+            s->c.completed++;
             s->queued--;
             continue;
         }
@@ -430,10 +719,17 @@ int khop_server_stats(khop_server *s, uint64_t *submitted, uint64_t *completed, 
                       uint64_t *batches_allocated) {
     if (!s) return KHOP_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    if (submitted) *submitted = s->submitted;
-    if (completed) *completed = s->completed;
-    if (steps) *steps = s->steps;
-    if (batches_allocated) *batches_allocated = s->slots_allocated;
+    if (submitted) *submitted = s->c.submitted;
+    if (completed) *completed = s->c.completed;
+    if (steps) *steps = s->c.steps;
+    if (batches_allocated) *batches_allocated = s->c.slots_allocated;
+    return KHOP_OK;
+}
+
+int khop_server_counters_get(khop_server *s, khop_server_counters *out) {
+    if (!s || !out) return KHOP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->c;
     return KHOP_OK;
 }
 
@@ -446,7 +742,7 @@ int khop_server_destroy(khop_server *s) {
         for (auto &r : s->inbox) {
             khop_result res{r.ticket, ~0ull, KHOP_ESHUTDOWN, r.k, r.t_submit, now_ns()};
             s->outbox.push_back(res);
-            s->completed++;
+            s->c.completed++;
             s->queued--;
         }
         s->inbox.clear();

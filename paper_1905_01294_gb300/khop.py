@@ -41,6 +41,7 @@ EXPORTS = [
     "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list", "khop_levels",
     "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
     "khop_server_destroy", "khop_graph_set_wait_limit", "khop_graph_test_absent_cta",
+    "khop_server_counters_get", "khop_server_set_wait_timeout",
 ]
 
 
@@ -67,13 +68,21 @@ class khop_query_stats(ctypes.Structure):
 
 class khop_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_batches", ctypes.c_uint32),
-                ("wait_timeout_us", ctypes.c_int64), ("max_pending", ctypes.c_uint32)]
+                ("wait_timeout_us", ctypes.c_int64), ("max_pending", ctypes.c_uint32),
+                ("admit_rounds", ctypes.c_uint32), ("plain_heavy", ctypes.c_int32)]
 
 
 class khop_result(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("count", ctypes.c_uint64),
                 ("status", ctypes.c_int32), ("k", ctypes.c_uint32),
                 ("t_submit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+class khop_server_counters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in (
+        "submitted", "completed", "steps", "slots_allocated", "joined_running", "retired_early",
+        "timed_out", "max_lanes_busy", "gpu_step_ns", "pull_steps", "clean_steps", "lane_steps",
+        "plain_launches")]
 
 
 QUERY_STATS_WORDS = ctypes.sizeof(khop_query_stats) // 8   # uint64 words per record
@@ -122,6 +131,8 @@ def lib():
                 "khop_server_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64)]),
                 "khop_server_destroy": (i32, [vp]),
+                "khop_server_counters_get": (i32, [vp, ctypes.POINTER(khop_server_counters)]),
+                "khop_server_set_wait_timeout": (i32, [vp, i64]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name, None)
@@ -279,6 +290,16 @@ def khop_server_stats(s):
     check(lib().khop_server_stats(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                   ctypes.byref(d)), "khop_server_stats")
     return dict(submitted=a.value, completed=b.value, steps=c.value, batches=d.value)
+
+
+def khop_server_counters_get(s) -> dict:
+    c = khop_server_counters()
+    check(lib().khop_server_counters_get(s, ctypes.byref(c)), "khop_server_counters_get")
+    return {f: getattr(c, f) for f, _ in khop_server_counters._fields_}
+
+
+def khop_server_set_wait_timeout(s, wait_timeout_us) -> None:
+    check(lib().khop_server_set_wait_timeout(s, wait_timeout_us), "khop_server_set_wait_timeout")
 
 
 def khop_server_destroy(s) -> None:
@@ -488,10 +509,13 @@ def stats_records(stats_tensor) -> np.ndarray:
 
 
 class Server:
-    """Continuous-batching request server (khop_server_*)."""
+    """Continuous-batching request server (khop_server_*): requests join the
+    rolling 64-lane traversals of its slots at round boundaries."""
 
-    def __init__(self, mem_budget_bytes=0, max_batches=0, wait_timeout_us=0, max_pending=0):
-        o = khop_server_opts(mem_budget_bytes, max_batches, wait_timeout_us, max_pending)
+    def __init__(self, mem_budget_bytes=0, max_batches=0, wait_timeout_us=0, max_pending=0,
+                 admit_rounds=0, plain_heavy=0):
+        o = khop_server_opts(mem_budget_bytes, max_batches, wait_timeout_us, max_pending,
+                             admit_rounds, plain_heavy)
         self.handle = khop_server_create(o)
 
     def submit(self, graph: Graph, seed: int, k: int) -> int:
@@ -522,6 +546,12 @@ class Server:
 
     def stats(self):
         return khop_server_stats(self.handle)
+
+    def counters(self) -> dict:
+        return khop_server_counters_get(self.handle)
+
+    def set_wait_timeout(self, wait_timeout_us: int) -> None:
+        khop_server_set_wait_timeout(self.handle, int(wait_timeout_us))
 
     def close(self):
         if getattr(self, "handle", None):

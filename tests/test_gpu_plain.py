@@ -194,7 +194,7 @@ def test_runs_of_small_1hop_queries():
 
 def test_fused_first_rounds_at_the_seed_degree_bound():
     """Multi-hop queries whose first two rounds run as one grid round (seed
-    out-degree up to 2048: every CTA lists the seed's distinct out-neighbours
+    out-degree up to 1024: every CTA lists the seed's distinct out-neighbours
     itself) and the ones just above the bound, with duplicate heads,
     self-loops, sinks among the neighbours, and heads that are also
     neighbours of neighbours; counts, TE and per-hop counts in all three
