@@ -629,6 +629,198 @@ def listing_leg(kh, torch, G, g, seeds, ks, counts, dev, stream):
             "levels_and_parents_per_s": len(pick) / (ms_l * 1e-3)}
 
 
+def measure(args, kh, torch, dev, dist, world, rank, local, g, G, wname, wkey, batched_nq, tuning,
+            steps, warmup, serving_kw=None, cpu_budget_s=25.0, directions=True, listing=True,
+            pool_sample=512):
+    """One workload measured on its resident graph G: the paper protocol on
+    the plain path (the headline metric's timed steps), its end-to-end form,
+    rooflines, and the batched, listing, direction and serving legs.  Returns
+    the JSON line's fields."""
+    seeds, ks = paper_queries(g)
+    nq = seeds.size
+    stream = torch.cuda.current_stream()
+    d_seeds = torch.from_numpy(seeds.view(np.int32)).to(dev)
+    d_ks = torch.from_numpy(ks.view(np.int32)).to(dev)
+    d_out = torch.empty(nq, dtype=torch.int64, device=dev)
+    d_te = torch.empty(nq, dtype=torch.int64, device=dev)
+    d_stats = torch.empty(nq * kh.QUERY_STATS_WORDS, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        kh.khop_count_ex(G.handle, d_seeds.data_ptr(), d_ks.data_ptr(), nq, d_out.data_ptr(),
+                         d_te.data_ptr(), d_stats.data_ptr(), None, 0, stream.cuda_stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ref_counts = kh.as_u64(d_out).copy()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    lat, te_sum, bytes_sum = [], 0, 0
+    lat_by_k = {k: [] for k, _ in PAPER_QUERIES}
+    bytes_by_k = {k: 0 for k, _ in PAPER_QUERIES}
+    for i in range(steps):
+        flush.fill_(i & 0xFF)                       # L2 flush between steps (not timed)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        evs[i][1].synchronize()
+        rec = kh.stats_records(d_stats)
+        dt = (rec["t_end_ns"] - rec["t_start_ns"]).astype(np.float64) * 1e-3
+        lat.extend(dt.tolist())
+        for k, _ in PAPER_QUERIES:
+            lat_by_k[k].extend(dt[ks == k].tolist())
+            bytes_by_k[k] += int(rec["bytes"][ks == k].sum())
+        te_sum += int(rec["te"].sum())
+        bytes_sum += int(rec["bytes"].sum())
+        if not np.array_equal(kh.as_u64(d_out), ref_counts):
+            raise SystemExit("counts changed between steps")
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_total, queries_total, value = over_ranks(dist, sum(step_ms) * 1e-3, nq * steps, dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    gteps = te_sum * world / t_total / 1e9
+
+    # e2e: public API, pinned host inputs, counts back to the host, per step
+    h_seeds = torch.from_numpy(seeds.view(np.int32)).pin_memory()
+    h_ks = torch.from_numpy(ks.view(np.int32)).pin_memory()
+    h_out = torch.empty(nq, dtype=torch.int64).pin_memory()
+    e_seeds = torch.empty_like(d_seeds)
+    e_ks = torch.empty_like(d_ks)
+    e_out = torch.empty_like(d_out)
+    e_t = 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_seeds.copy_(h_seeds, non_blocking=True)
+        e_ks.copy_(h_ks, non_blocking=True)
+        kh.khop_count_mixed(G.handle, e_seeds.data_ptr(), e_ks.data_ptr(), nq, e_out.data_ptr(),
+                            kh.MODE_PLAIN, stream.cuda_stream)
+        h_out.copy_(e_out, non_blocking=True)
+        stream.synchronize()
+        e_t += time.perf_counter() - t0
+        if not np.array_equal(h_out.numpy().view(np.uint64), ref_counts):
+            raise SystemExit("e2e counts differ")
+    _, _, e2e_qps = over_ranks(dist, e_t, nq * steps, dev)
+    e2e = {"value": e2e_qps, "unit": "queries/s",
+           "h2d_bytes_per_step": int(seeds.nbytes + ks.nbytes),
+           "d2h_bytes_per_step": int(nq * 8)}
+
+    peak, peak_kind = load_peaks()
+    achieved = bytes_sum / t_total / 1e9   # per GPU: one rank's kernel bytes over the max time
+    traffic = captured_traffic("plain_kernel", wkey)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "plain_kernel (persistent push/pull traversal)",
+                "peak_kind": peak_kind,
+                # the captured DRAM bytes per step over this run's mean step time
+                "dram_gbs": (traffic / (t_total / steps) / 1e9) if traffic else None}
+    # push-equivalent bytes: |{u : dist(s, u) < k}| = count(s, k - 1) + 1, from
+    # one untimed plain call at k - 1; TE from the last timed step
+    try:   # an auxiliary figure: the headline line is printed whatever happens here
+        d_kp = torch.from_numpy((np.maximum(ks, 1) - 1).astype(np.uint32).view(np.int32)).to(dev)
+        d_cp = torch.empty(nq, dtype=torch.int64, device=dev)
+        kh.khop_count_mixed(G.handle, d_seeds.data_ptr(), d_kp.data_ptr(), nq, d_cp.data_ptr(),
+                            kh.MODE_PLAIN, stream.cuda_stream)
+        torch.cuda.synchronize()
+        b_ref = push_equivalent_bytes(kh.as_u64(d_te), kh.as_u64(d_cp).astype(np.float64) + 1.0,
+                                      4 if g.nnz < 2**32 else 8)
+        a_ref = b_ref * steps / t_total / 1e9
+        roofline["push_equivalent"] = {"bytes_per_step": b_ref, "achieved": a_ref,
+                                       "frac": a_ref / peak}
+    except Exception as exc:   # noqa: BLE001
+        print(f"push-equivalent bytes not computed: {exc}", file=sys.stderr)
+        roofline["push_equivalent"] = None
+    # per k: the queries' algorithmic bytes over their device-timestamp latencies
+    roofline_by_k = {}
+    for k, _ in PAPER_QUERIES:
+        t_k = float(np.sum(lat_by_k[k])) * 1e-6
+        if t_k > 0:
+            a_k = bytes_by_k[k] / t_k / 1e9
+            roofline_by_k[str(k)] = {"achieved": a_k, "frac": a_k / peak,
+                                     "bytes_per_query": bytes_by_k[k] / max(1, len(lat_by_k[k]))}
+
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, steps, warmup,
+                                        flush, peak, nq=batched_nq, gname=wname.split(" ")[0],
+                                        wkey=wkey)
+        if listing:
+            extras["listing"] = listing_leg(kh, torch, G, g, seeds, ks, ref_counts, dev, stream)
+        if directions:
+            extras["directions"] = variants_leg(kh, torch, dev, stream, args.scale, steps,
+                                                warmup, flush)
+        if serving_kw is not None:
+            mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
+            extras["serving"] = serving_leg(kh, G, g, mean_by_k, **serving_kw)
+    lat_p = percentiles(lat)
+    line = {
+        "metric": "k-hop queries/sec (plain sequential, paper protocol)",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": workload_config(wname, g, nq, world),
+        "tuning": tuning,
+        "gteps": gteps,
+        "latency_us": lat_p,
+        "latency_us_by_k": {str(k): percentiles(v) for k, v in lat_by_k.items()},
+        "e2e": e2e,
+        "roofline": roofline,
+        "roofline_by_k": roofline_by_k,
+        "gpu_launches": steps,   # one persistent plain_kernel launch per step
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g, seeds, ks, budget_s=cpu_budget_s)
+        if "batched" in line:
+            try:   # an auxiliary baseline: the headline line is printed whatever happens here
+                line["batched"]["cpu_pool"] = cpu_pool_baseline(
+                    g, gen.seeds(g, batched_nq, seed=2), gen.mixed_ks(batched_nq, seed=2),
+                    sample=pool_sample)
+            except Exception as exc:   # noqa: BLE001
+                print(f"thread-pool oracle baseline not measured: {exc}", file=sys.stderr)
+    return line
+
+
+def power_law_leg(args, kh, torch, dev, dist, world, rank, local, G2, g2):
+    """The 41.6M-vertex, 1.47e9-edge power-law graph (read from the on-disk
+    cache when present): the paper protocol on the plain path, 1024 batched
+    queries, and serving with both graphs resident (20k requests per rate)."""
+    t0 = time.time()
+    gl = gen.cached("chunglu", **CHUNGLU)
+    t_gen = time.time() - t0
+    GL = kh.Graph.from_csr(gl)
+    t = GL.autotune(gen.seeds(gl, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    tuning = {f: (getattr(t, f) if isinstance(getattr(t, f), int) else round(getattr(t, f), 3))
+              for f, _ in t._fields_}
+    name = (f"chunglu-n41.6M-m{gl.nnz}-wmax3e6-seed4 directed plain 300/300/10/10 seeds "
+            f"k=1/2/3/6")
+    sub = measure(args, kh, torch, dev, dist, world, rank, local, gl, GL, name, "chunglu", 1024,
+                  tuning, min(args.steps, 5), min(args.warmup, 3),
+                  serving_kw=None if args.no_serving else dict(
+                      G2=G2, g2=g2, nreq=20000, rates=(5e3, 10e3, 20e3, 40e3, 80e3, 160e3),
+                      names="chunglu-41.6M/1.47e9 and kronecker-s21"),
+                  cpu_budget_s=10.0, directions=False, listing=False, pool_sample=64)
+    sub["graph_load_s"] = t_gen
+    GL.close()
+    return sub
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,6 +834,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="plain path only")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the power-law (41.6M-vertex) leg of the default run")
     ap.add_argument("--case", choices=["plain6", "batch6"],
                     help="run one launch of a small case (for a profiler) and exit: plain6 = "
                          "10 six-hop queries on the plain path, batch6 = 128 six-hop queries "
@@ -682,170 +876,21 @@ def main():
                           "counts_head": kh.as_u64(out)[:4].tolist()}))
         G.close()
         return 0
-    stream = torch.cuda.current_stream()
-    d_seeds = torch.from_numpy(seeds.view(np.int32)).to(dev)
-    d_ks = torch.from_numpy(ks.view(np.int32)).to(dev)
-    d_out = torch.empty(nq, dtype=torch.int64, device=dev)
-    d_te = torch.empty(nq, dtype=torch.int64, device=dev)
-    d_stats = torch.empty(nq * kh.QUERY_STATS_WORDS, dtype=torch.int64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def step():
-        kh.khop_count_ex(G.handle, d_seeds.data_ptr(), d_ks.data_ptr(), nq, d_out.data_ptr(),
-                         d_te.data_ptr(), d_stats.data_ptr(), None, 0, stream.cuda_stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ref_counts = kh.as_u64(d_out).copy()
-
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        pass
-    sampler = ClockSampler(uuid) if rank == 0 else None
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    lat, te_sum, bytes_sum = [], 0, 0
-    lat_by_k = {k: [] for k, _ in PAPER_QUERIES}
-    bytes_by_k = {k: 0 for k, _ in PAPER_QUERIES}
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)                       # L2 flush between steps (not timed)
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-        evs[i][1].synchronize()
-        rec = kh.stats_records(d_stats)
-        dt = (rec["t_end_ns"] - rec["t_start_ns"]).astype(np.float64) * 1e-3
-        lat.extend(dt.tolist())
-        for k, _ in PAPER_QUERIES:
-            lat_by_k[k].extend(dt[ks == k].tolist())
-            bytes_by_k[k] += int(rec["bytes"][ks == k].sum())
-        te_sum += int(rec["te"].sum())
-        bytes_sum += int(rec["bytes"].sum())
-        if not np.array_equal(kh.as_u64(d_out), ref_counts):
-            raise SystemExit("counts changed between steps")
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_total, queries_total, value = over_ranks(dist, sum(step_ms) * 1e-3, nq * args.steps, dev)
-    if dist is not None:
-        dist.barrier()
-    clocks = sampler.stop() if sampler else None
-    gteps = te_sum * world / t_total / 1e9
-
-    # e2e: public API, pinned host inputs, counts back to the host, per step
-    h_seeds = torch.from_numpy(seeds.view(np.int32)).pin_memory()
-    h_ks = torch.from_numpy(ks.view(np.int32)).pin_memory()
-    h_out = torch.empty(nq, dtype=torch.int64).pin_memory()
-    e_seeds = torch.empty_like(d_seeds)
-    e_ks = torch.empty_like(d_ks)
-    e_out = torch.empty_like(d_out)
-    e_t = 0.0
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e_seeds.copy_(h_seeds, non_blocking=True)
-        e_ks.copy_(h_ks, non_blocking=True)
-        kh.khop_count_mixed(G.handle, e_seeds.data_ptr(), e_ks.data_ptr(), nq, e_out.data_ptr(),
-                            kh.MODE_PLAIN, stream.cuda_stream)
-        h_out.copy_(e_out, non_blocking=True)
-        stream.synchronize()
-        e_t += time.perf_counter() - t0
-        if not np.array_equal(h_out.numpy().view(np.uint64), ref_counts):
-            raise SystemExit("e2e counts differ")
-    _, _, e2e_qps = over_ranks(dist, e_t, nq * args.steps, dev)
-    e2e = {"value": e2e_qps, "unit": "queries/s",
-           "h2d_bytes_per_step": int(seeds.nbytes + ks.nbytes),
-           "d2h_bytes_per_step": int(nq * 8)}
-
-    peak, peak_kind = load_peaks()
-    achieved = bytes_sum / t_total / 1e9   # per GPU: one rank's kernel bytes over the max time
-    traffic = captured_traffic("plain_kernel", args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "plain_kernel (persistent push/pull traversal)",
-                "peak_kind": peak_kind,
-                # the captured DRAM bytes per step over this run's mean step time
-                "dram_gbs": (traffic / (t_total / args.steps) / 1e9) if traffic else None}
-    # push-equivalent bytes: |{u : dist(s, u) < k}| = count(s, k - 1) + 1, from
-    # one untimed plain call at k - 1; TE from the last timed step
-    try:   # an auxiliary figure: the headline line is printed whatever happens here
-        d_kp = torch.from_numpy((np.maximum(ks, 1) - 1).astype(np.uint32).view(np.int32)).to(dev)
-        d_cp = torch.empty(nq, dtype=torch.int64, device=dev)
-        kh.khop_count_mixed(G.handle, d_seeds.data_ptr(), d_kp.data_ptr(), nq, d_cp.data_ptr(),
-                            kh.MODE_PLAIN, stream.cuda_stream)
-        torch.cuda.synchronize()
-        b_ref = push_equivalent_bytes(kh.as_u64(d_te), kh.as_u64(d_cp).astype(np.float64) + 1.0,
-                                      4 if g.nnz < 2**32 else 8)
-        a_ref = b_ref * args.steps / t_total / 1e9
-        roofline["push_equivalent"] = {"bytes_per_step": b_ref, "achieved": a_ref,
-                                       "frac": a_ref / peak}
-    except Exception as exc:   # noqa: BLE001
-        print(f"push-equivalent bytes not computed: {exc}", file=sys.stderr)
-        roofline["push_equivalent"] = None
-    # per k: the queries' algorithmic bytes over their device-timestamp latencies
-    roofline_by_k = {}
-    for k, _ in PAPER_QUERIES:
-        t_k = float(np.sum(lat_by_k[k])) * 1e-6
-        if t_k > 0:
-            a_k = bytes_by_k[k] / t_k / 1e9
-            roofline_by_k[str(k)] = {"achieved": a_k, "frac": a_k / peak,
-                                     "bytes_per_query": bytes_by_k[k] / max(1, len(lat_by_k[k]))}
-
-    extras = {}
-    if not args.no_extras:
-        extras["batched"] = batched_leg(kh, torch, G, g, dev, stream, args.steps, args.warmup,
-                                        flush, peak, nq=batched_nq, gname=wname.split(" ")[0],
-                                        wkey=args.workload)
-        extras["listing"] = listing_leg(kh, torch, G, g, seeds, ks, ref_counts, dev, stream)
-        if args.workload == "kronecker21":
-            extras["directions"] = variants_leg(kh, torch, dev, stream, args.scale, args.steps,
-                                                args.warmup, flush)
-        if not args.no_serving:
-            mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
-            if args.workload == "chunglu":
-                g2, _ = workload_graph(21)
-                G2 = kh.Graph.from_csr(g2)
-                # the power-law graph's 6-hop queries take ~1 ms: start the sweep lower
-                extras["serving"] = serving_leg(kh, G, g, mean_by_k, G2=G2, g2=g2,
-                                                rates=(5e3, 10e3, 20e3, 40e3, 80e3, 160e3),
-                                                names="chunglu-41.6M/1.47e9 and kronecker-s21")
-                G2.close()
-            else:
-                extras["serving"] = serving_leg(kh, G, g, mean_by_k, names=wname.split(" ")[0])
-    lat_p = percentiles(lat)
-    line = {
-        "metric": "k-hop queries/sec (plain sequential, paper protocol)",
-        "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": workload_config(wname, g, nq, world),
-        "tuning": tuning,
-        "gteps": gteps,
-        "latency_us": lat_p,
-        "latency_us_by_k": {str(k): percentiles(v) for k, v in lat_by_k.items()},
-        "e2e": e2e,
-        "roofline": roofline,
-        "roofline_by_k": roofline_by_k,
-        "gpu_launches": args.steps,   # one persistent plain_kernel launch per step
-        "clocks": clocks,
-    }
-    line.update(extras)
-    if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(g, seeds, ks)
-        if "batched" in line:
-            try:   # an auxiliary baseline: the headline line is printed whatever happens here
-                line["batched"]["cpu_pool"] = cpu_pool_baseline(
-                    g, gen.seeds(g, batched_nq, seed=2), gen.mixed_ks(batched_nq, seed=2),
-                    sample=512 if args.workload == "kronecker21" else 128)
-            except Exception as exc:   # noqa: BLE001
-                print(f"thread-pool oracle baseline not measured: {exc}", file=sys.stderr)
+    line = measure(args, kh, torch, dev, dist, world, rank, local, g, G, wname, args.workload,
+                   batched_nq, tuning, args.steps, args.warmup,
+                   serving_kw=None if (args.no_extras or args.no_serving) else (
+                       dict(names=wname.split(" ")[0]) if args.workload == "kronecker21" else
+                       dict(G2=None, names=wname.split(" ")[0], rates=(5e3, 10e3, 20e3, 40e3, 80e3))),
+                   directions=args.workload == "kronecker21",
+                   pool_sample=512 if args.workload == "kronecker21" else 128)
+    if args.workload == "kronecker21" and not args.no_extras and not args.no_large:
+        # the Twitter-shaped power-law graph (41.6M vertices, 1.47e9 edges), with
+        # the scale-21 graph still resident for two-graph serving
+        try:
+            line["chunglu"] = power_law_leg(args, kh, torch, dev, dist, world, rank, local, G, g)
+        except Exception as exc:   # noqa: BLE001 -- the headline line is printed regardless
+            print(f"power-law leg not measured: {exc}", file=sys.stderr)
+            line["chunglu"] = {"unavailable": str(exc)[:300]}
     if rank == 0:
         print(json.dumps(line))
     G.close()

@@ -32,6 +32,7 @@ constexpr int kPushUnroll = 4;
 constexpr int kDeferEdges = 4096;    // longer in-lists go to the chunked pass
 constexpr int kChunk = 4096;         // in-edges per chunk of the chunked pass
 constexpr int kPlanes = 4;           // bit-sliced counter planes (up to 15 additions)
+constexpr bool kVecIdx = true;       // pull: a lane reads its in-list four indices per 16-byte load
 constexpr int kStage = 2048;
 constexpr int kStagePosShift = 40;
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
@@ -503,16 +504,45 @@ __device__ __forceinline__ void pull_round(const BatchArgs<E, LW> &a, const Roun
             const bool go = needs && pos < e && !lcovers(acc, need);
             if (!__any_sync(FULL, go)) break;
             uint32_t u[kPullILP];
+            E took = 0;
+            if (kVecIdx) {
+                // the kPullILP/4 aligned 16-byte blocks of in-edge indices from
+                // the block holding pos: one vector load per four indices (the
+                // list's unaligned head and tail are masked off); the array's
+                // last partial block is read index by index
+                const E base = pos & ~(E)3;
+                const E end = min(base + (E)kPullILP, e);
 #pragma unroll
-            for (int t = 0; t < kPullILP; ++t) u[t] = (go && pos + t < e) ? a.ri[pos + t] : kEmpty;
+                for (int t = 0; t < kPullILP; t += 4) {
+                    uint32_t q[4] = {kEmpty, kEmpty, kEmpty, kEmpty};
+                    const E at = base + (E)t;
+                    if (go && at < end) {
+                        if ((uint64_t)at + 4 <= a.nnz) {
+                            const uint4 v4 = *reinterpret_cast<const uint4 *>(a.ri + at);
+                            q[0] = v4.x; q[1] = v4.y; q[2] = v4.z; q[3] = v4.w;
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if ((uint64_t)at + j < a.nnz) q[j] = a.ri[at + j];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const E x = at + (E)j;
+                        u[t + j] = (go && x >= pos && x < end) ? q[j] : kEmpty;
+                    }
+                }
+                if (go) took = end - pos;
+            } else {
+#pragma unroll
+                for (int t = 0; t < kPullILP; ++t) u[t] = (go && pos + t < e) ? a.ri[pos + t] : kEmpty;
+                if (go) took = min((E)kPullILP, e - pos);
+            }
 #pragma unroll
             for (int t = 0; t < kPullILP; ++t)
                 if (u[t] != kEmpty) lor_into(acc, R.Fin[u[t]]);
-            if (go) {
-                const E took = min((E)kPullILP, e - pos);
-                pos += took;
-                scanned += (uint64_t)took;
-            }
+            pos += took;
+            scanned += (uint64_t)took;
         }
         const bool open = needs && pos < e && !lcovers(acc, need);
         const bool defer = open && (uint64_t)(e - pos) > (uint64_t)kDeferEdges;
