@@ -763,6 +763,7 @@ def measure(args, kh, torch, dev, dist, world, rank, local, g, G, wname, wkey, b
         if directions:
             extras["directions"] = variants_leg(kh, torch, dev, stream, args.scale, steps,
                                                 warmup, flush)
+            extras["mxv"] = mxv_leg(kh, torch, G, g, stream, steps, flush, peak)
         if serving_kw is not None:
             mean_by_k = {k: float(np.mean(v)) for k, v in lat_by_k.items()}
             extras["serving"] = serving_leg(kh, G, g, mean_by_k, **serving_kw)
@@ -819,6 +820,56 @@ def power_law_leg(args, kh, torch, dev, dist, world, rank, local, G2, g2):
     sub["graph_load_s"] = t_gen
     GL.close()
     return sub
+
+
+def mxv_leg(kh, torch, G, g, stream, steps, flush, peak):
+    """khop_mxv over the whole graph for each semiring (x: seeded random
+    values, a third of them the "no entry" identity; no mask), and OR_AND as
+    a BFS step (the frontier at distance 2 from a seed, the visited set as the
+    complemented mask).  Algorithmic bytes per call: 2W n (column offsets) +
+    8 n (y) + (4 + 8) per in-edge examined (index, x gather) + n/8 (mask)."""
+    rng = np.random.default_rng(11)
+    W = 4 if g.nnz < 2**32 else 8
+    res = {"workload": f"{g.n} vertices, {g.nnz} edges, one call per step, L2 flushed between steps",
+           "unit": "calls/s"}
+    cases = []
+    for sr, name in ((kh.SR_OR_AND, "or_and"), (kh.SR_PLUS_TIMES, "plus_times"),
+                     (kh.SR_MIN_SECOND, "min_second"), (kh.SR_MAX_SECOND, "max_second")):
+        x = rng.integers(1, 2**40, g.n, dtype=np.uint64)
+        x[rng.random(g.n) < 0.33] = np.uint64(2**64 - 1) if sr == kh.SR_MIN_SECOND else np.uint64(0)
+        cases.append((name, sr, torch.from_numpy(x.view(np.int64)).cuda(), None))
+    s0 = int(gen.seeds(g, 1, seed=13)[0])
+    lv, _ = G.levels(s0, 2, parents=False)
+    lvh = lv.cpu().numpy()
+    q = (lvh == 2).astype(np.uint64)
+    vis = np.nonzero(lvh >= 0)[0]
+    words = np.zeros((g.n + 31) // 32, np.uint32)
+    np.bitwise_or.at(words, vis >> 5, np.uint32(1) << (vis & 31).astype(np.uint32))
+    cases.append(("or_and_bfs_step", kh.SR_OR_AND, torch.from_numpy(q.view(np.int64)).cuda(),
+                  torch.from_numpy(words.view(np.int32)).cuda()))
+    y = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for name, sr, xd, md in cases:
+        call = lambda: kh.khop_mxv(G.handle, sr, xd.data_ptr(), md.data_ptr() if md is not None else None,
+                                   1 if md is not None else 0, y.data_ptr(), stream.cuda_stream)
+        call()
+        torch.cuda.synchronize()
+        scanned = kh.khop_mxv_stats(G.handle)
+        ms = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        t = ms * 1e-3 / steps
+        byts = 2 * W * g.n + 8 * g.n + 12 * scanned + (g.n // 8 if md is not None else 0)
+        ach = byts / t / 1e9
+        res[name] = {"value": 1.0 / t, "us_per_call": t * 1e6, "in_edges_scanned": scanned,
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak}}
+    return res
 
 
 def main():

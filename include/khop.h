@@ -209,6 +209,41 @@ int khop_levels(khop_graph *g, uint32_t seed, uint32_t k, int32_t *out_levels,
                 uint32_t *out_parents, void *stream);
 
 /*
+ * One masked matrix-vector product over a semiring, the building block the
+ * paper's Sec. II runs every traversal with (the k-hop count is the (OR, AND)
+ * case iterated, masked by the complement of the visited set):
+ *     y[v] = (+)_{u : A[u][v] = 1} x[u] (x) 1     for the vertices v the mask selects,
+ *     y[v] = the (+)-identity                       for the others,
+ * i.e. y = A^T x over in-edges (on a KHOP_REVERSE / KHOP_UNDIRECTED graph the
+ * in-edges of the stored direction, as for every count).
+ *   semiring   KHOP_SR_OR_AND:     y[v] = 1 if some in-neighbour u has x[u] != 0, else 0
+ *              KHOP_SR_PLUS_TIMES: y[v] = sum of x[u] over the in-edges, mod 2^64
+ *                                  (iterated from e_s: the number of walks of each length)
+ *              KHOP_SR_MIN_SECOND: y[v] = min of x[u] over the in-edges, UINT64_MAX if
+ *                                  none (x[u] = u on a frontier: BFS parents)
+ *              KHOP_SR_MAX_SECOND: y[v] = max of x[u] over the in-edges, 0 if none
+ *   x          device uint64[n]; the (+)-identity (0; UINT64_MAX for MIN) means "no entry"
+ *   mask       device uint32 bitmap [ceil(n/32)] (bit v of word v/32) or NULL = all
+ *              vertices; mask_complement != 0 selects the vertices whose bit is clear
+ *   y          device uint64[n], written whole; may not alias x
+ * Sums run over the stored in-edges: an edge given twice to khop_graph_create
+ * adds twice.  Asynchronous on `stream`, ordered with the graph's other calls.
+ * Errors: EINVAL (NULL graph / x / y, unknown semiring), ECUDA.
+ */
+enum khop_semiring {
+    KHOP_SR_OR_AND = 0,
+    KHOP_SR_PLUS_TIMES = 1,
+    KHOP_SR_MIN_SECOND = 2,
+    KHOP_SR_MAX_SECOND = 3
+};
+int khop_mxv(khop_graph *g, int semiring, const uint64_t *x, const uint32_t *mask, int mask_complement,
+             uint64_t *y, void *stream);
+
+/* In-edges examined by the last khop_mxv call on g (read it before the next
+ * call on g; synchronises the device). */
+int khop_mxv_stats(khop_graph *g, uint64_t *scanned);
+
+/*
  * The k-hop neighbourhood itself -- the visited set v_k of Sec. III, the seed
  * included -- rather than its size, for one query on the plain path.
  *   khop_neighbourhood: bit v of out_bits (ceil(n/32) uint32 words, device

@@ -116,3 +116,45 @@ def bfs_parents(g, s: int, k: int) -> np.ndarray:
     np.minimum.at(par, dst[ok], src[ok].astype(np.uint64))
     par[s] = s
     return par.astype(np.uint32)
+
+
+# ---- masked matrix-vector products over semirings ----------------------------
+
+SR_OR_AND, SR_PLUS_TIMES, SR_MIN_SECOND, SR_MAX_SECOND = 0, 1, 2, 3
+U64MAX = np.uint64(2**64 - 1)
+
+
+def mxv(g, semiring: int, x, mask=None, complement: bool = False) -> np.ndarray:
+    """y = A^T x over a semiring, edge by edge (Sec. II: a traversal step is a
+    sparse matrix-vector product): for every stored edge u -> v the term
+    x[u] (x) 1 is folded into y[v] with the semiring's (+); vertices the mask
+    does not select, and vertices with no in-edge, keep the (+)-identity.
+      OR_AND: y[v] = 1 if some u -> v has x[u] != 0;  PLUS_TIMES: sum of x[u]
+      mod 2^64;  MIN_SECOND / MAX_SECOND: min / max of x[u].
+    mask: uint32 bitmap (bit v of word v // 32) or None; complement selects
+    the clear bits.  A plain loop over the edge list (numpy ufunc.at)."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(rp))
+    dst = np.asarray(g.col_idx[: int(rp[-1])], dtype=np.int64)
+    if semiring == SR_OR_AND:
+        y = np.zeros(g.n, dtype=np.uint64)
+        np.bitwise_or.at(y, dst, (x[src] != 0).astype(np.uint64))
+    elif semiring == SR_PLUS_TIMES:
+        y = np.zeros(g.n, dtype=np.uint64)
+        np.add.at(y, dst, x[src])          # uint64: wraps mod 2^64
+    elif semiring == SR_MIN_SECOND:
+        y = np.full(g.n, U64MAX, dtype=np.uint64)
+        np.minimum.at(y, dst, x[src])
+    elif semiring == SR_MAX_SECOND:
+        y = np.zeros(g.n, dtype=np.uint64)
+        np.maximum.at(y, dst, x[src])
+    else:
+        raise ValueError("unknown semiring")
+    if mask is not None:
+        m = np.asarray(mask, dtype=np.uint32)
+        bits = ((m[np.arange(g.n) >> 5] >> (np.arange(g.n) & 31).astype(np.uint32)) & 1).astype(bool)
+        sel = ~bits if complement else bits
+        ident = U64MAX if semiring == SR_MIN_SECOND else np.uint64(0)
+        y[~sel] = ident
+    return y

@@ -29,6 +29,8 @@ HOST_PTRS, DEVICE_PTRS, SYMMETRIC, VALIDATE, WIDE_OFFSETS = 0, 1, 2, 4, 8
 REVERSE, UNDIRECTED = 16, 32
 # directions and modes
 DIR_AUTO, DIR_PUSH, DIR_PULL = 0, 1, 2
+# semirings of khop_mxv
+SR_OR_AND, SR_PLUS_TIMES, SR_MIN_SECOND, SR_MAX_SECOND = 0, 1, 2, 3
 MODE_AUTO, MODE_PLAIN, MODE_BATCHED64, MODE_BATCHED128, MODE_BATCHED256 = 0, 1, 2, 3, 4
 
 UINT64_MAX = (1 << 64) - 1
@@ -41,7 +43,7 @@ EXPORTS = [
     "khop_batch_stats", "khop_neighbourhood", "khop_neighbourhood_list", "khop_levels",
     "khop_server_create", "khop_submit", "khop_submit_many", "khop_poll", "khop_server_stats",
     "khop_server_destroy", "khop_graph_set_wait_limit", "khop_graph_test_absent_cta",
-    "khop_server_counters_get", "khop_server_set_wait_timeout",
+    "khop_server_counters_get", "khop_server_set_wait_timeout", "khop_mxv", "khop_mxv_stats",
 ]
 
 
@@ -118,6 +120,8 @@ def lib():
                 "khop_count_static": (i32, [u64, vp, vp, vp, vp, u64, vp, u64, u32, vp, vp]),
                 "khop_get_error": (i32, [vp, ctypes.POINTER(u32)]),
                 "khop_graph_set_wait_limit": (i32, [vp, u64]),
+                "khop_mxv": (i32, [vp, i32, vp, vp, i32, vp, vp]),
+                "khop_mxv_stats": (i32, [vp, ctypes.POINTER(u64)]),
                 "khop_graph_test_absent_cta": (i32, [vp, u32]),
                 "khop_neighbourhood": (i32, [vp, u32, u32, vp, vp, vp]),
                 "khop_neighbourhood_list": (i32, [vp, u32, u32, vp, u64, vp, vp]),
@@ -237,6 +241,16 @@ def khop_get_error(g) -> int:
     bits = ctypes.c_uint32()
     check(lib().khop_get_error(g, ctypes.byref(bits)), "khop_get_error")
     return bits.value
+
+
+def khop_mxv(g, semiring, x, mask, mask_complement, y, stream) -> None:
+    check(lib().khop_mxv(g, semiring, x, mask, mask_complement, y, stream), "khop_mxv")
+
+
+def khop_mxv_stats(g) -> int:
+    v = ctypes.c_uint64()
+    check(lib().khop_mxv_stats(g, ctypes.byref(v)), "khop_mxv_stats")
+    return v.value
 
 
 def khop_graph_set_wait_limit(g, timeout_ns) -> None:
@@ -488,6 +502,25 @@ class Graph:
         khop_levels(self.handle, int(seed), int(k), lv.data_ptr(),
                     par.data_ptr() if parents else None, _stream_ptr(stream))
         return lv, par
+
+    def mxv(self, semiring, x, mask=None, complement=False, stream=None):
+        """y = A^T x over `semiring` (a khop_mxv call).  x: uint64 values
+        (numpy array or CUDA int64 tensor); mask: a bitmap of ceil(n/32)
+        words (numpy uint32 or CUDA int32 tensor) or None.  Returns y as a
+        CUDA int64 tensor holding uint64 values."""
+        torch = self._torch
+        if isinstance(x, np.ndarray):
+            xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint64).view(np.int64)).cuda()
+        else:
+            xt = x.contiguous()
+        mt = None
+        if mask is not None:
+            mt = (torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint32).view(np.int32)).cuda()
+                  if isinstance(mask, np.ndarray) else mask.contiguous())
+        y = torch.empty(self.n, dtype=torch.int64, device="cuda")
+        khop_mxv(self.handle, int(semiring), xt.data_ptr(), mt.data_ptr() if mt is not None else None,
+                 1 if complement else 0, y.data_ptr(), _stream_ptr(stream))
+        return y
 
     def autotune(self, seeds, k=None, ks=None, stream=None) -> khop_tuning:
         """Tune on these seeds with one k for all, or per-seed ks."""

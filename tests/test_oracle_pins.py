@@ -333,3 +333,114 @@ def test_levels_and_parents_against_networkx_bfs():
                 assert par[v] == min(preds)
             else:
                 assert par[v] == 0xFFFFFFFF
+
+
+# ---- masked matrix-vector products over semirings --------------------------
+
+def _mult_matrix(g):
+    """Dense edge-multiplicity matrix M[u, v] = number of stored edges u -> v."""
+    M = np.zeros((g.n, g.n), dtype=np.int64)
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    src = np.repeat(np.arange(g.n), np.diff(rp))
+    np.add.at(M, (src, np.asarray(g.col_idx[: int(rp[-1])], dtype=np.int64)), 1)
+    return M
+
+
+def test_mxv_plus_times_iterated_counts_walks_like_matrix_powers():
+    """PLUS_TIMES applied k times to e_s gives the number of walks of length k
+    from s to each vertex: row s of M^k (numpy's matrix power of the
+    multiplicity matrix; parallel edges are distinct walks)."""
+    rng = np.random.default_rng(21)
+    for trial in range(12):
+        n = int(rng.integers(2, 40))
+        m = int(rng.integers(0, 4 * n))
+        g = gen.csr_raw(n, rng.integers(0, n, m), rng.integers(0, n, m))   # duplicates, self-loops
+        M = _mult_matrix(g)
+        for s in rng.choice(n, min(n, 4), replace=False):
+            x = np.zeros(n, np.uint64)
+            x[s] = 1
+            for k in range(1, 6):
+                x = oracle.mxv(g, oracle.SR_PLUS_TIMES, x)
+                want = np.linalg.matrix_power(M, k)[s]
+                np.testing.assert_array_equal(x.astype(np.int64), want)
+
+
+def test_mxv_plus_times_wraps_mod_2_64():
+    g = gen.csr_raw(3, [0, 1], [2, 2])
+    x = np.array([2**63, 2**63 + 5, 0], np.uint64)
+    y = oracle.mxv(g, oracle.SR_PLUS_TIMES, x)
+    assert y.tolist() == [0, 0, 5]
+
+
+def test_mxv_or_and_with_complemented_visited_mask_is_a_bfs_step():
+    """Iterating q <- (A^T q) AND NOT v, v <- v OR q from e_s with OR_AND and the
+    visited set as the complemented mask gives the vertices at each hop
+    distance exactly (the k-hop count's own iteration), checked against the
+    oracle's BFS distances and the matrix-power reach sets."""
+    for g in (gen.rmat(8, 8, seed=3), gen.rmat(8, 8, seed=4, symmetrize=True)):
+        A = brute.dense_from_csr(g)
+        R = brute.reach_powers(A[None], 6)
+        for s in (0, 5, 17, 200):
+            d = oracle.khop_dist(g, s, 6)
+            q = np.zeros(g.n, np.uint64)
+            q[s] = 1
+            vis = q.copy()
+            for r in range(1, 7):
+                words = np.zeros((g.n + 31) // 32, np.uint32)
+                idx = np.nonzero(vis)[0]
+                np.bitwise_or.at(words, idx >> 5, (np.uint32(1) << (idx & 31).astype(np.uint32)))
+                q = oracle.mxv(g, oracle.SR_OR_AND, q, mask=words, complement=True)
+                np.testing.assert_array_equal(np.nonzero(q)[0], np.nonzero(d == r)[0])
+                reach = R[r - 1][0, s] | (np.arange(g.n) == s)
+                prev = (R[r - 2][0, s] if r >= 2 else np.zeros(g.n, bool)) | (np.arange(g.n) == s)
+                np.testing.assert_array_equal(q.astype(bool), reach & ~prev)
+                vis = vis | q
+
+
+def test_mxv_min_and_max_second_give_extreme_predecessors():
+    """With x[u] = u on the frontier {u : dist(u) = r}, MIN_SECOND / MAX_SECOND
+    masked to the unvisited vertices give, for every vertex at distance r+1,
+    its smallest / largest in-neighbour at distance r (networkx BFS)."""
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(23)
+    for _ in range(15):
+        n = int(rng.integers(2, 50))
+        m = int(rng.integers(0, 4 * n))
+        src, dst = rng.integers(0, n, m), rng.integers(0, n, m)
+        g = gen.csr_raw(n, src, dst)
+        G = nx.DiGraph()
+        G.add_nodes_from(range(n))
+        G.add_edges_from(zip(src.tolist(), dst.tolist()))
+        s = int(rng.integers(0, n))
+        dist = nx.single_source_shortest_path_length(G, s)
+        for r in range(0, 4):
+            front = [u for u, d in dist.items() if d == r]
+            x_min = np.full(n, 2**64 - 1, np.uint64)
+            x_max = np.zeros(n, np.uint64)
+            x_min[front] = front
+            x_max[front] = front
+            words = np.zeros((n + 31) // 32, np.uint32)
+            for u, d in dist.items():
+                if d <= r:
+                    words[u >> 5] |= np.uint32(1) << np.uint32(u & 31)
+            y_min = oracle.mxv(g, oracle.SR_MIN_SECOND, x_min, mask=words, complement=True)
+            y_max = oracle.mxv(g, oracle.SR_MAX_SECOND, x_max, mask=words, complement=True)
+            for v in range(n):
+                preds = [u for u in G.predecessors(v) if dist.get(u) == r]
+                if dist.get(v, -1) == r + 1:
+                    assert y_min[v] == min(preds) and y_max[v] == max(preds)
+                elif dist.get(v, 99) <= r:          # masked out: the identity
+                    assert y_min[v] == 2**64 - 1 and y_max[v] == 0
+
+
+def test_mxv_mask_selects_outputs():
+    g = gen.rmat(7, 8, seed=5)
+    x = np.arange(g.n, dtype=np.uint64) + 1
+    words = np.random.default_rng(1).integers(0, 2**32, (g.n + 31) // 32, dtype=np.uint64).astype(np.uint32)
+    bits = ((words[np.arange(g.n) >> 5] >> (np.arange(g.n) & 31).astype(np.uint32)) & 1).astype(bool)
+    full = oracle.mxv(g, oracle.SR_PLUS_TIMES, x)
+    for comp in (False, True):
+        y = oracle.mxv(g, oracle.SR_PLUS_TIMES, x, mask=words, complement=comp)
+        sel = ~bits if comp else bits
+        np.testing.assert_array_equal(y[sel], full[sel])
+        assert (y[~sel] == 0).all()
