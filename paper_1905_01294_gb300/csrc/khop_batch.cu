@@ -32,7 +32,11 @@ constexpr int kPushUnroll = 4;
 constexpr int kDeferEdges = 4096;    // longer in-lists go to the chunked pass
 constexpr int kChunk = 4096;         // in-edges per chunk of the chunked pass
 constexpr int kPlanes = 4;           // bit-sliced counter planes (up to 15 additions)
+#ifdef KHOP_SCALAR_INDEX_LOADS
+constexpr bool kVecIdx = false;      // the 4-byte-load build, kept for before/after measurements
+#else
 constexpr bool kVecIdx = true;       // pull: a lane reads its in-list four indices per 16-byte load
+#endif
 constexpr int kStage = 2048;
 constexpr int kStagePosShift = 40;
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;

@@ -45,7 +45,8 @@ using namespace khop;
 
 constexpr uint64_t kMarginBytes = 1ull << 30;
 constexpr int kLanes = 64;
-constexpr size_t kHeavySlots = 2;    // rolling slots per graph at most
+constexpr size_t kHeavySlots = 3;    // rolling slots per graph at most (three steps and a plain
+                                     // launch are resident at once)
 constexpr size_t kPlainSlots = 2;    // plain slots per graph at most
 constexpr int kPlainBatch = 16;      // light requests per plain launch at most
 constexpr uint32_t kAdmitWindow = 1; // default: a rolling slot admits while its lanes have run <= 1 round
@@ -66,6 +67,10 @@ struct Request {
 };
 
 bool light(uint32_t k) { return k <= 2; }
+// Queue of a request: 0 light, 1 heavy of depth 3, 2 deeper.  A rolling slot
+// serves one depth class at a time, so its lanes finish at about the same
+// round and the slot drains (and refills) without idling on a few deep lanes.
+int queue_of(uint32_t k) { return light(k) ? 0 : (k <= 3 ? 1 : 2); }
 
 struct Lane {
     bool used = false;     // holds a request
@@ -88,6 +93,7 @@ struct Slot {
     Lane lane[kLanes];
     int used = 0;                  // lanes in use
     int ndirty = 0;                // lanes waiting to be cleaned
+    int queue = 0;                 // the heavy queue (1 or 2) it serves while lanes are in use
     bool busy = false;             // a step is in flight
     bool lost = false;             // that step was given up: its requests already failed
     bool reset = false;            // the next step starts from zeroed state
@@ -109,7 +115,9 @@ struct PlainSlot {
 
 struct GraphCtx {
     khop_graph *g = nullptr;
-    std::deque<Request> pending[2];   // light, heavy
+    std::deque<Request> pending[3];   // light, heavy of depth 3, deeper
+    bool heavy_waiting() const { return !pending[1].empty() || !pending[2].empty(); }
+    size_t heavy_pending() const { return pending[1].size() + pending[2].size(); }
     std::vector<Slot *> slots;
     std::vector<PlainSlot *> pslots;
     bool alloc_failed = false;       // the last rolling-slot allocation was refused
@@ -275,14 +283,28 @@ int free_lanes(const Slot *sl) {
 // do, so a traversal whose lanes went deep takes no new lanes until it drains.
 void admit(khop_server *s, GraphCtx *ctx, Slot *sl) {
     int nfree = free_lanes(sl);
-    std::deque<Request> &q = ctx->pending[1];
-    if (nfree == 0 || q.empty()) return;
+    if (nfree == 0 || !ctx->heavy_waiting()) return;
+    if (sl->used == 0) {   // an empty slot serves the queue with the oldest request
+        const bool a = !ctx->pending[1].empty(), b = !ctx->pending[2].empty();
+        sl->queue = (a && (!b || ctx->pending[1].front().t_submit <= ctx->pending[2].front().t_submit)) ? 1 : 2;
+    }
+    // with one slot per graph (max_batches = 1) it serves both depth classes
+    const bool shared = s->opts.max_batches == 1;
+    if (!shared && ctx->pending[sl->queue].empty()) return;
     for (const Lane &ln : sl->lane)
         if (ln.used && ln.rounds > s->admit_rounds) return;
     const bool running = sl->used > 0;
     int l = 0;
     uint64_t joined = 0;
-    while (!q.empty() && nfree > 0) {
+    while (nfree > 0) {
+        std::deque<Request> *qp = &ctx->pending[sl->queue];
+        if (shared) {   // the older head of the two queues
+            std::deque<Request> &a = ctx->pending[1], &b = ctx->pending[2];
+            if (a.empty() && b.empty()) break;
+            qp = (!a.empty() && (b.empty() || a.front().t_submit <= b.front().t_submit)) ? &a : &b;
+        }
+        std::deque<Request> &q = *qp;
+        if (q.empty()) break;
         while (!lane_free(sl->lane[l])) ++l;
         --nfree;
         Lane &ln = sl->lane[l];
@@ -317,7 +339,7 @@ void launch_step(khop_server *s, GraphCtx *ctx, Slot *sl) {
         if ((uint64_t)ln.rounds + 1 >= (uint64_t)ln.req.k) p.fin |= 1ull << l;
     }
     // lanes run short while requests wait: clear the retired lanes' marks now
-    p.clean_dense = (p.clean != 0ull && !ctx->pending[1].empty() && free_lanes(sl) <= kLanes / 2) ? 1u : 0u;
+    p.clean_dense = (p.clean != 0ull && ctx->heavy_waiting() && free_lanes(sl) <= kLanes / 2) ? 1u : 0u;
     p.pull_ok = 1u;   // lanes of a slot are within kAdmitWindow + 1 rounds of each other
     p.reset = sl->reset ? 1u : 0u;
     sl->reset = false;
@@ -451,7 +473,7 @@ void worker_main(khop_server *s) {
                 ctx = new GraphCtx();
                 ctx->g = r.g;
             }
-            ctx->pending[light(r.k) ? 0 : 1].push_back(r);
+            ctx->pending[queue_of(r.k)].push_back(r);
         }
         incoming.clear();
         const uint64_t timeout_ns = (uint64_t)s->timeout_us.load() * 1000ull;
@@ -529,9 +551,10 @@ void worker_main(khop_server *s) {
             // light requests first; heavy ones too while only a few wait
             const auto plain_cls = [&]() {
                 if (!ctx->pending[0].empty()) return 0;
-                if (!ctx->pending[1].empty() && s->plain_heavy >= 0 &&
-                    ctx->pending[1].size() <= (size_t)s->plain_heavy)
-                    return 1;
+                if (ctx->heavy_waiting() && s->plain_heavy >= 0 && ctx->heavy_pending() <= (size_t)s->plain_heavy) {
+                    const bool a = !ctx->pending[1].empty(), b = !ctx->pending[2].empty();
+                    return (a && (!b || ctx->pending[1].front().t_submit <= ctx->pending[2].front().t_submit)) ? 1 : 2;
+                }
                 return -1;
             };
             for (PlainSlot *ps : ctx->pslots) {
@@ -557,13 +580,13 @@ void worker_main(khop_server *s) {
                 // all of its lanes wait for cleaning while requests wait: a
                 // step that only clears their marks
                 const bool need_clean = sl->ndirty > 0 && sl->used == 0 && free_lanes(sl) <= kLanes / 2 &&
-                                        !ctx->pending[1].empty();
+                                        ctx->heavy_waiting();
                 if (sl->used > 0 || need_clean) {
                     launch_step(s, ctx, sl);
                     launched = true;
                 }
             }
-            while (!ctx->pending[1].empty() && !ctx->alloc_failed) {
+            while (ctx->heavy_waiting() && !ctx->alloc_failed) {
                 Slot *sl = try_alloc_slot(s, ctx);
                 if (!sl) {
                     ctx->alloc_failed = true;
@@ -579,11 +602,13 @@ void worker_main(khop_server *s) {
                 ctx->pending[0].clear();
             }
             if (ctx->slots.empty() && ctx->alloc_failed) {
-                for (auto &r : ctx->pending[1]) post(s, r, ~0ull, KHOP_ENOMEM);
-                ctx->pending[1].clear();
+                for (int qi = 1; qi <= 2; ++qi) {
+                    for (auto &r : ctx->pending[qi]) post(s, r, ~0ull, KHOP_ENOMEM);
+                    ctx->pending[qi].clear();
+                }
             }
             if (ctx->pending[0].empty()) ctx->palloc_failed = false;   // try again next time
-            if (ctx->pending[1].empty()) ctx->alloc_failed = false;
+            if (!ctx->heavy_waiting()) ctx->alloc_failed = false;
         }
         // poll again at once while launches run or requests came lately: a
         // timed sleep or a condition-variable wake-up here costs tens of
