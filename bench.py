@@ -887,10 +887,12 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the power-law (41.6M-vertex) leg of the default run")
-    ap.add_argument("--case", choices=["plain6", "batch6"],
+    ap.add_argument("--case", choices=["plain6", "batch6", "mxv"],
                     help="run one launch of a small case (for a profiler) and exit: plain6 = "
                          "10 six-hop queries on the plain path, batch6 = 128 six-hop queries "
-                         "(two 64-lane batches)")
+                         "(two 64-lane batches), mxv = two PLUS_TIMES khop_mxv calls over the graph "
+                         "(the first also lists the hub chunks: plan, vertex and chunk kernels, "
+                         "then vertex and chunk kernels)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -918,6 +920,14 @@ def main():
         t = G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
         tuning = {f: (getattr(t, f) if isinstance(getattr(t, f), int) else round(getattr(t, f), 3))
                   for f, _ in t._fields_}
+    if args.case == "mxv":
+        x = np.random.default_rng(11).integers(1, 2**40, g.n, dtype=np.uint64)
+        y = G.mxv(kh.SR_PLUS_TIMES, x)
+        y = G.mxv(kh.SR_PLUS_TIMES, x)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "mxv", "y_head": kh.as_u64(y)[:4].tolist()}))
+        G.close()
+        return 0
     if args.case:
         cs = gen.seeds(g, 128 if args.case == "batch6" else 10, seed=2)
         out = G.count_mixed(cs, np.full(cs.size, 6, np.uint32),

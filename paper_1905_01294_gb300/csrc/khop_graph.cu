@@ -274,6 +274,8 @@ void free_graph(khop_graph *g) {
     free_batch_state(g->batch);
     free_batch_state(g->batch2);
     free_batch_state(g->batch4);
+    cudaFree(g->mxv_cv);
+    cudaFree(g->mxv_cs);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
 }

@@ -363,6 +363,11 @@ struct khop_graph {
     int last_lw = 1;                        // lane width of the last batched call
 
     khop_tuning tune{};
+    // khop_mxv: the in-lists longer than kMxvLong, cut into chunks (built on first use)
+    uint32_t *mxv_cv = nullptr;             // vertex of each chunk
+    unsigned long long *mxv_cs = nullptr;   // first in-edge of each chunk
+    uint64_t mxv_nch = 0;                   // chunks
+    bool mxv_ready = false;
     uint64_t timeout_ns = 2000000000ull;   // bound of every device wait (grid barriers)
     unsigned absent_at = 0;                // testing: see khop_graph_test_absent_cta
     uint64_t device_bytes = 0;

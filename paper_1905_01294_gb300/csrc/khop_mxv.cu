@@ -13,9 +13,16 @@
 // The sums run over the stored in-edges, so a duplicated edge adds twice.
 // One warp takes 32 consecutive vertices (a coalesced read of their column
 // offsets and mask word); each lane folds its vertex's first in-edges itself
-// (four index loads in flight), then the warp folds the longer lists one
-// vertex at a time, 32 lanes wide, and reduces across lanes with shuffles.
-// OR_AND stops a list at its first hit.
+// (four index loads in flight), then the warp folds the lists of up to
+// kMxvLong edges one vertex at a time, 32 lanes wide, and reduces across
+// lanes with shuffles.  Longer in-lists (the hubs of a power-law graph, which
+// hold much of the edges) are cut into chunks of at most kMxvChunk edges,
+// listed once per graph; a second kernel folds each chunk with one warp
+// (coalesced index loads, eight in flight per lane) and combines the warp's
+// result into y[v] with one atomic, so no warp walks a hub's list alone and
+// no CTA waits on another's barrier.  OR_AND stops a list at its first hit.
+#include <algorithm>
+
 #include "khop_internal.cuh"
 
 namespace khop {
@@ -29,6 +36,7 @@ struct Semiring<KHOP_SR_OR_AND> {
     __device__ static unsigned long long add(unsigned long long a, unsigned long long b) { return a | (b != 0ull); }
     __device__ static unsigned long long join(unsigned long long a, unsigned long long b) { return a | b; }
     __device__ static bool done(unsigned long long a) { return a != 0ull; }
+    __device__ static void combine(unsigned long long *p, unsigned long long a) { atomicOr(p, a); }
 };
 template <>
 struct Semiring<KHOP_SR_PLUS_TIMES> {
@@ -36,6 +44,7 @@ struct Semiring<KHOP_SR_PLUS_TIMES> {
     __device__ static unsigned long long add(unsigned long long a, unsigned long long b) { return a + b; }
     __device__ static unsigned long long join(unsigned long long a, unsigned long long b) { return a + b; }
     __device__ static bool done(unsigned long long) { return false; }
+    __device__ static void combine(unsigned long long *p, unsigned long long a) { atomicAdd(p, a); }
 };
 template <>
 struct Semiring<KHOP_SR_MIN_SECOND> {
@@ -43,6 +52,7 @@ struct Semiring<KHOP_SR_MIN_SECOND> {
     __device__ static unsigned long long add(unsigned long long a, unsigned long long b) { return b < a ? b : a; }
     __device__ static unsigned long long join(unsigned long long a, unsigned long long b) { return b < a ? b : a; }
     __device__ static bool done(unsigned long long) { return false; }
+    __device__ static void combine(unsigned long long *p, unsigned long long a) { atomicMin(p, a); }
 };
 template <>
 struct Semiring<KHOP_SR_MAX_SECOND> {
@@ -50,9 +60,19 @@ struct Semiring<KHOP_SR_MAX_SECOND> {
     __device__ static unsigned long long add(unsigned long long a, unsigned long long b) { return b > a ? b : a; }
     __device__ static unsigned long long join(unsigned long long a, unsigned long long b) { return b > a ? b : a; }
     __device__ static bool done(unsigned long long) { return false; }
+    __device__ static void combine(unsigned long long *p, unsigned long long a) { atomicMax(p, a); }
 };
 
-constexpr int kLaneList = 32;   // in-edges a lane folds alone before the warp helps
+#ifndef KHOP_MXV_LONG
+#define KHOP_MXV_LONG 256
+#endif
+#ifndef KHOP_MXV_CHUNK
+#define KHOP_MXV_CHUNK 1024
+#endif
+constexpr int kLaneList = 32;                   // in-edges a lane folds alone before the warp helps
+constexpr uint64_t kMxvLong = KHOP_MXV_LONG;    // longer in-lists go to the chunk kernel
+constexpr uint64_t kMxvChunk = KHOP_MXV_CHUNK;  // in-edges per chunk (one warp's task)
+constexpr int kChunkLoads = 8;                  // index loads in flight per lane
 
 template <typename E, int SR>
 __global__ void __launch_bounds__(256) mxv_kernel(const E *cp, const uint32_t *ri, const unsigned long long *x,
@@ -71,6 +91,7 @@ __global__ void __launch_bounds__(256) mxv_kernel(const E *cp, const uint32_t *r
         if (on) {
             b = cp[v];
             e = cp[v + 1];
+            if ((uint64_t)(e - b) > kMxvLong) on = false;   // the chunk kernel folds it
         }
         unsigned long long acc = S::zero;
         E pos = b;
@@ -113,13 +134,117 @@ __global__ void __launch_bounds__(256) mxv_kernel(const E *cp, const uint32_t *r
     if (lane == 0 && scanned) atomicAdd(scanned_out, (unsigned long long)scanned);
 }
 
+// The long in-lists, chunk by chunk: one warp folds a chunk (kChunkLoads
+// coalesced index loads in flight per lane), reduces across its lanes and
+// combines the result into y[v] atomically (y[v] was set to the identity by
+// mxv_kernel, earlier on the same stream).
+template <typename E, int SR>
+__global__ void __launch_bounds__(256) mxv_chunk_kernel(const E *cp, const uint32_t *ri, const unsigned long long *x,
+                                                        const uint32_t *mask, unsigned comp, const uint32_t *cv,
+                                                        const unsigned long long *cs, uint64_t nch,
+                                                        unsigned long long *y, unsigned long long *scanned_out) {
+    using S = Semiring<SR>;
+    constexpr uint64_t kStep = 32 * kChunkLoads;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t scanned = 0;
+    for (uint64_t c = gwarp; c < nch; c += nwarps) {
+        const uint32_t v = cv[c];
+        // lane 0 decides for the warp: a vertex outside the mask, or (OR_AND) one
+        // another chunk has already set, is skipped
+        int skip = 0;
+        if (lane == 0) {
+            skip = mask && ((((mask[v >> 5] >> (v & 31)) & 1u) ^ comp) == 0u);
+            if (SR == KHOP_SR_OR_AND && !skip) skip = *(volatile unsigned long long *)&y[v] != 0ull;
+        }
+        if (__shfl_sync(FULL, skip, 0)) continue;
+        const uint64_t b = cs[c];
+        const uint64_t e = min(b + kMxvChunk, (uint64_t)cp[v + 1]);
+        unsigned long long acc = S::zero;
+        for (uint64_t q = b; q < e; q += kStep) {
+            uint32_t u[kChunkLoads];
+#pragma unroll
+            for (int t = 0; t < kChunkLoads; ++t) {
+                const uint64_t p = q + (uint64_t)(t * 32 + lane);
+                u[t] = p < e ? ri[p] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int t = 0; t < kChunkLoads; ++t)
+                if (u[t] != 0xffffffffu) acc = S::add(acc, x[u[t]]);
+            scanned += min(kStep, e - q);
+            if (SR == KHOP_SR_OR_AND && __any_sync(FULL, acc != 0ull)) break;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = S::join(acc, __shfl_xor_sync(FULL, acc, o));
+        if (lane == 0 && acc != S::zero) S::combine(&y[v], acc);
+    }
+    if (lane == 0 && scanned) atomicAdd(scanned_out, (unsigned long long)scanned);
+}
+
+// Chunks of the in-lists longer than kMxvLong, in any order.
+template <typename E>
+__global__ void mxv_plan_kernel(const E *cp, uint64_t n, uint32_t *cv, unsigned long long *cs, uint64_t cap,
+                                unsigned long long *count) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint64_t b = cp[v], d = (uint64_t)cp[v + 1] - b;
+        if (d <= kMxvLong) continue;
+        const uint64_t nch = (d + kMxvChunk - 1) / kMxvChunk;
+        const unsigned long long at = atomicAdd(count, (unsigned long long)nch);
+        for (uint64_t i = 0; i < nch && at + i < cap; ++i) {
+            cv[at + i] = (uint32_t)v;
+            cs[at + i] = b + i * kMxvChunk;
+        }
+    }
+}
+
+// Build the graph's chunk list on first use (allocates; synchronises `st`).
+template <typename E>
+int ensure_plan(khop_graph *g, cudaStream_t st) {
+    if (g->mxv_ready) return KHOP_OK;
+    // each long list has more than kMxvLong edges (at most nnz / kMxvLong of
+    // them) and adds at most one partial chunk to its nnz-share of whole ones
+    const uint64_t cap = g->nnz / kMxvChunk + g->nnz / kMxvLong + 1;
+    unsigned long long *cnt = &g->plain.ctl->pad[1];
+    cudaError_t e = cudaMalloc(&g->mxv_cv, cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g->mxv_cs, cap * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        mxv_plan_kernel<E><<<g->num_sms * 4, 256, 0, st>>>((const E *)g->cp, g->n, g->mxv_cv, g->mxv_cs, cap, cnt);
+        e = cudaGetLastError();
+    }
+    unsigned long long nch = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nch, cnt, sizeof(nch), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(g->mxv_cv);
+        cudaFree(g->mxv_cs);
+        g->mxv_cv = nullptr;
+        g->mxv_cs = nullptr;
+        return cuda_status(e);
+    }
+    g->mxv_nch = nch < cap ? nch : cap;
+    g->device_bytes += cap * (sizeof(uint32_t) + sizeof(unsigned long long));
+    g->mxv_ready = true;
+    return KHOP_OK;
+}
+
 template <typename E, int SR>
 int launch_sr(khop_graph *g, const uint64_t *x, const uint32_t *mask, int comp, uint64_t *y, cudaStream_t st) {
     const int blocks = g->num_sms * 8;
     mxv_kernel<E, SR><<<blocks, 256, 0, st>>>((const E *)g->cp, g->ri, (const unsigned long long *)x, mask,
                                               comp ? 1u : 0u, g->n, g->nw, (unsigned long long *)y,
                                               &g->plain.ctl->pad[0]);
-    return cuda_status(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && g->mxv_nch) {
+        const uint64_t cb = std::min<uint64_t>((g->mxv_nch + 7) / 8, (uint64_t)g->num_sms * 8);
+        mxv_chunk_kernel<E, SR><<<(unsigned)cb, 256, 0, st>>>(
+            (const E *)g->cp, g->ri, (const unsigned long long *)x, mask, comp ? 1u : 0u, g->mxv_cv, g->mxv_cs,
+            g->mxv_nch, (unsigned long long *)y, &g->plain.ctl->pad[0]);
+        e = cudaGetLastError();
+    }
+    return cuda_status(e);
 }
 
 template <typename E>
@@ -145,6 +270,8 @@ extern "C" int khop_mxv(khop_graph *g, int semiring, const uint64_t *x, const ui
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = order_after_previous(g, st);
     // the in-edges scanned, for khop_mxv_stats (the plain control block's spare word)
+    if (rc == KHOP_OK)
+        rc = g->ewidth == 4 ? ensure_plan<uint32_t>(g, st) : ensure_plan<unsigned long long>(g, st);
     if (rc == KHOP_OK) rc = cuda_status(cudaMemsetAsync(&g->plain.ctl->pad[0], 0, sizeof(unsigned long long), st));
     if (rc == KHOP_OK)
         rc = g->ewidth == 4 ? launch_mxv<uint32_t>(g, semiring, x, mask, mask_complement, y, st)
