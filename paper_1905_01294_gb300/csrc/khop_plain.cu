@@ -35,7 +35,7 @@ constexpr uint32_t kFuseDeg = 1024;          // seeds with at most this many out
 constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
                                              // vertices are visited) read V before test-and-set
 constexpr int kPullWords = 2;    // bitmap words a warp works on at once in a pull round
-constexpr int kFlatILP = 4;      // in-edges per lane per step of the flattened pull scan
+constexpr int kFlatILP = 2;      // in-edges per lane per step of the flattened pull scan
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
 constexpr int kStagePosShift = 40;                       // staged count above, edges below
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
@@ -105,6 +105,7 @@ struct Round {
                              // set (or the seed) are skipped
     const uint32_t *nbr;     // fused: hash set of the seed's distinct out-neighbours
     uint32_t level;          // the round's number (its discoveries are at that hop distance)
+    uint32_t rot;            // rotation of the push tiles over CTAs 1 .. G-1 (same in every CTA)
 };
 
 // Per-CTA shared state of a round.
@@ -119,6 +120,7 @@ struct Shared {
     int qfull;                   // this CTA saw the queue past its cap (pull rounds)
     unsigned long long slot[4];  // counters of the round just finished
     unsigned m1;                 // fused round: distinct out-neighbours of the seed
+    unsigned pdeg;               // row length of the prelude held in the hash tables
     uint64_t ring_q;             // thread 0: the query whose ring_advance is due next
     int flag;
 };
@@ -302,9 +304,15 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
     const uint32_t tl = a.tile_log2;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
-    // CTA 0 writes the query results between queries: it takes tile G - 1,
-    // and CTA c > 0 takes tile c - 1 (small rounds have one tile).
-    const uint64_t rank = blockIdx.x == 0 ? gridDim.x - 1u : blockIdx.x - 1u;
+    // CTA 0 writes the query results between queries: it takes tile G - 1.
+    // CTAs 1 .. G-1 take tiles 0 .. G-2 in an order rotated every round, so
+    // the few tiles of a small round go to CTAs other than the previous
+    // round's workers (which arrive last at its barrier and list the next
+    // query's prelude only then).
+    const uint32_t g1 = gridDim.x - 1u;
+    uint32_t rk = blockIdx.x - 1u + R.rot;   // R.rot < max(g1, 1)
+    if (rk >= g1) rk -= g1;
+    const uint64_t rank = blockIdx.x == 0 ? (uint64_t)g1 : (uint64_t)rk;
     for (uint64_t j = rank; j < ntiles; j += gridDim.x) {
         const uint64_t e0 = j << tl;
         const uint64_t e1 = min(e0 + T, R.mf);
@@ -394,72 +402,107 @@ __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E>
 // each key's first position.  The row offsets of every position are loaded
 // alongside the inserts (a repeated head just loads its row twice), and one
 // scan over the threads -- which hold consecutive positions -- gives both each
-// kept head's index and its prefix.  Returns m1 (both tables are emptied by
-// the caller after the round).
+// kept head's index and its prefix.  `pslot` records the slot of every row
+// position and sh.pdeg the row length, so prelude_clear empties only those
+// slots.  Returns m1 (the caller empties the tables after the round).
 template <typename E, int BLOCK>
 __device__ __forceinline__ uint32_t fused_prelude(const PlainArgs<E> &a, uint32_t s, E rs0,
-                                                  uint32_t deg, uint32_t *tab, uint32_t *pos, E *s_pre,
-                                                  E *s_rs, Shared &sh) {
+                                                  uint32_t deg, uint32_t *tab, uint32_t *pos, uint16_t *pslot,
+                                                  E *s_pre, E *s_rs, Shared &sh) {
     constexpr int kPer = (int)(kFuseDeg / BLOCK);
+    constexpr uint32_t kWarpPos = 32u * (uint32_t)kPer;   // row positions a warp holds
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ unsigned long long s_wtot[32];   // per warp: kept count << 40 | edge sum
-    // thread t holds row positions t * kPer .. t * kPer + kPer - 1
+    // thread t holds row positions t * kPer .. t * kPer + kPer - 1; warps whose
+    // positions all lie past the row's end only join the barriers
+    const uint32_t na = (deg + kWarpPos - 1u) / kWarpPos;
+    const bool active = (uint32_t)warp < na;
     uint32_t w[kPer], slot[kPer];
     E rsv[kPer], rev[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-        const uint32_t e = threadIdx.x * kPer + u;
-        w[u] = e < deg ? a.ci[(uint64_t)rs0 + e] : kHashEmpty;
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
+        w[u] = kHashEmpty;
+        slot[u] = kHashSlots;
         rsv[u] = 0;
         rev[u] = 0;
-        if (w[u] != kHashEmpty) {
-            rsv[u] = a.rp[w[u]];
-            rev[u] = a.rp[w[u] + 1];
-        }
     }
+    if (active) {
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        slot[u] = kHashSlots;
-        if (w[u] != kHashEmpty && w[u] != s) {
-            hash_insert_at(tab, w[u], slot[u]);
-            atomicMin(&pos[slot[u]], threadIdx.x * kPer + u);
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t e = threadIdx.x * kPer + u;
+            if (e < deg) w[u] = a.ci[(uint64_t)rs0 + e];
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if (w[u] != kHashEmpty) {
+                rsv[u] = a.rp[w[u]];
+                rev[u] = a.rp[w[u] + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if (w[u] != kHashEmpty && w[u] != s) {
+                hash_insert_at(tab, w[u], slot[u]);
+                atomicMin(&pos[slot[u]], threadIdx.x * kPer + u);
+            }
+            if (threadIdx.x * kPer + u < deg) pslot[threadIdx.x * kPer + u] = (uint16_t)slot[u];
         }
     }
+    if (threadIdx.x == 0) sh.pdeg = deg;
     __syncthreads();
     // keep each neighbour at its first position: (count, edges) of this thread
     unsigned keep = 0;
-    unsigned long long mine = 0;
+    unsigned long long mine = 0, incl = 0;
+    if (active) {
 #pragma unroll
-    for (int u = 0; u < kPer; ++u)
-        if (slot[u] < kHashSlots && pos[slot[u]] == threadIdx.x * kPer + u) {
-            keep |= 1u << u;
-            mine += (1ull << 40) + (unsigned long long)(rev[u] - rsv[u]);
-        }
-    const unsigned long long incl = warp_inclusive_sum(mine);
-    if (lane == 31) s_wtot[warp] = incl;
-    __syncthreads();
-    unsigned long long base = incl - mine, tot = 0;
-    for (int i = 0; i < BLOCK / 32; ++i) {
-        if (i < warp) base += s_wtot[i];
-        tot += s_wtot[i];
+        for (int u = 0; u < kPer; ++u)
+            if (slot[u] < kHashSlots && pos[slot[u]] == threadIdx.x * kPer + u) {
+                keep |= 1u << u;
+                mine += (1ull << 40) + (unsigned long long)(rev[u] - rsv[u]);
+            }
+        incl = warp_inclusive_sum(mine);
+        if (lane == 31) s_wtot[warp] = incl;
     }
-    uint32_t idx = (uint32_t)(base >> 40);
-    E pre = (E)(base & ((1ull << 40) - 1ull));
+    __syncthreads();
+    if (warp == 0) {   // inclusive scan of the active warps' totals
+        unsigned long long x = (uint32_t)lane < na ? s_wtot[lane] : 0ull;
+        x = warp_inclusive_sum(x);
+        if ((uint32_t)lane < na) s_wtot[lane] = x;
+    }
+    __syncthreads();
+    const unsigned long long tot = na ? s_wtot[na - 1u] : 0ull;
+    if (active) {
+        const unsigned long long base = incl - mine + (warp ? s_wtot[warp - 1] : 0ull);
+        uint32_t idx = (uint32_t)(base >> 40);
+        E pre = (E)(base & ((1ull << 40) - 1ull));
 #pragma unroll
-    for (int u = 0; u < kPer; ++u)
-        if ((keep >> u) & 1u) {
-            s_pre[idx] = pre;
-            s_rs[idx] = rsv[u];
-            pre += rev[u] - rsv[u];
-            ++idx;
-        }
+        for (int u = 0; u < kPer; ++u)
+            if ((keep >> u) & 1u) {
+                s_pre[idx] = pre;
+                s_rs[idx] = rsv[u];
+                pre += rev[u] - rsv[u];
+                ++idx;
+            }
+    }
     const uint32_t m1 = (uint32_t)(tot >> 40);
     if (threadIdx.x == 0) s_pre[m1] = (E)(tot & ((1ull << 40) - 1ull));
     __syncthreads();
     return m1;
+}
+
+// Empty the prelude's hash set and first-position table: only the slots its
+// row positions filled (a repeated head empties its slot twice).
+template <int BLOCK>
+__device__ __forceinline__ void prelude_clear(uint32_t *tab, uint32_t *pos, const uint16_t *pslot,
+                                              const Shared &sh) {
+    const uint32_t deg = sh.pdeg;
+    for (uint32_t p = threadIdx.x; p < deg; p += BLOCK) {
+        const uint32_t sl = pslot[p];
+        if (sl < kHashSlots) {
+            tab[sl] = kHashEmpty;
+            pos[sl] = 0xffffffffu;
+        }
+    }
 }
 
 // Pull round (masked SpMV over the unvisited vertices).  Warp w owns the
@@ -866,6 +909,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     E *st_d = st_rs + kStage;
     uint32_t *s_nbr = (uint32_t *)(st_d + kStage);    // fused rounds: hash set [kHashSlots]
     uint32_t *s_npos = s_nbr + kHashSlots;            //   and each key's first row position
+    uint16_t *s_pslot = (uint16_t *)(s_npos + kHashSlots);   //   and each row position's slot [kFuseDeg]
     __shared__ Shared sh;
     __shared__ E s_winc[BLOCK], s_wpos[BLOCK];        // flattened pull scan, 32 per warp
     __shared__ Peek<E> s_ring[kRing];                 // look-ahead over the query list
@@ -878,6 +922,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         sh.limit = ~0ull;
         sh.skipped = 0;
         sh.qfull = 0;
+        sh.pdeg = 0;
     }
     uint64_t t_prev = b0 ? globaltimer_ns() : 0;
     BarState bsense = barrier_start(&a.ctl->bar, a.absent_at);
@@ -903,6 +948,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
     if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, nullptr, nullptr, 0, a.timeout_ns)) return;
 
     uint64_t rdone = 0;   // rounds run in this launch (selects the rotating buffers)
+    uint32_t rot = 0;     // push tile rotation (see push_round)
     unsigned par = 0;     // which visited bitmap the current query uses
     bool pre_have = false;   // the current query's fused prelude already ran
     uint32_t pre_m1 = 0;     //   (at the previous query's last barrier) and its m1
@@ -950,6 +996,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         int prev = DIR_PUSH;
         for (uint32_t r = 1; r <= k && mf > 0; ++r) {
             ++rdone;
+            rot += 7u;   // the tile rotation of this round, below max(G - 1, 1)
+            while (rot >= max(gridDim.x - 1u, 1u)) rot -= max(gridDim.x - 1u, 1u);
             const unsigned iin = (unsigned)((rdone - 1) % 3), iout = (unsigned)(rdone % 3);
             const unsigned izero = (unsigned)((rdone + 1) % 3);
             const unsigned qin = (unsigned)((rdone - 1) & 1), qout = (unsigned)(rdone & 1);
@@ -984,24 +1032,23 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             bool fused = false;
             if (r == 1 && k >= 2 && !all_pull && a.stage && mf <= (uint64_t)kFuseDeg) {
                 m1 = pre_have ? pre_m1
-                              : fused_prelude<E, BLOCK>(a, s, cur.rs, (uint32_t)mf, s_nbr, s_npos, s_pre, s_rs, sh);
+                              : fused_prelude<E, BLOCK>(a, s, cur.rs, (uint32_t)mf, s_nbr, s_npos, s_pslot, s_pre,
+                                                        s_rs, sh);
                 pre_have = false;
                 mf2 = (uint64_t)s_pre[m1];
                 const uint64_t mu = a.nnz - (mf + mf2);
                 fused = a.direction == KHOP_DIR_PUSH || !fx_gt(mf2, a.alpha_fx, mu);
                 if (fused && blockIdx.x == 0)   // q_1 visited (round 2 skips it)
-                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
-                        const uint32_t x = s_nbr[i];
-                        if (x != kHashEmpty) {
+                    for (uint32_t p = threadIdx.x; p < sh.pdeg; p += BLOCK) {
+                        const uint32_t sl = s_pslot[p];
+                        if (sl < kHashSlots) {
+                            const uint32_t x = s_nbr[sl];
                             atomicOr(&V[x >> 5], 1u << (x & 31));
                             if (a.levels) a.levels[x] = 1;
                         }
                     }
                 if (!fused) {
-                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
-                        s_nbr[i] = kHashEmpty;
-                        s_npos[i] = 0xffffffffu;
-                    }
+                    prelude_clear<BLOCK>(s_nbr, s_npos, s_pslot, sh);
                     __syncthreads();
                 }
             }
@@ -1012,6 +1059,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.fused = fused;
             R.nbr = s_nbr;
             R.level = fused ? 2u : r;
+            R.rot = rot;
             R.seed = s;
             R.seed_rs = cur.rs;
             R.V = V;
@@ -1054,14 +1102,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             const auto pre_next = [&]() {
                 if (!do_pre) return;
                 if (fused) {
-                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
-                        s_nbr[i] = kHashEmpty;
-                        s_npos[i] = 0xffffffffu;
-                    }
+                    prelude_clear<BLOCK>(s_nbr, s_npos, s_pslot, sh);
                     __syncthreads();
                 }
                 pre_m1 = fused_prelude<E, BLOCK>(a, nxt.s, nxt.rs, (uint32_t)(nxt.re - nxt.rs), s_nbr, s_npos,
-                                                 s_pre, s_rs, sh);
+                                                 s_pslot, s_pre, s_rs, sh);
             };
             if (!grid_barrier(&a.ctl->bar, &a.ctl->err, &sh.flag, bsense, slots + kSlotWords * iout, sh.slot,
                               (R.last && blockIdx.x != 0) ? 0 : 4, a.timeout_ns, prefetch_next, pre_next))
@@ -1074,11 +1119,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             const uint64_t items_out = R.last ? 0 : min((uint64_t)(qp >> a.ebits), R.cap);
             if (fused) {
                 // rounds 1 and 2: q_1 (m1 vertices) was listed by every CTA
-                if (!do_pre)
-                    for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) {
-                        s_nbr[i] = kHashEmpty;
-                        s_npos[i] = 0xffffffffu;
-                    }
+                if (!do_pre) prelude_clear<BLOCK>(s_nbr, s_npos, s_pslot, sh);
                 bytes += 4ull * mf + (2ull * W + 4ull) + 4ull * m1;                   // round 1
                 bytes += 4ull * mf2 + (2ull * W + 4ull) * m1 + 4ull * items_out;      // round 2
                 te += mf2;
@@ -1144,11 +1185,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
 }
 
 // Dynamic shared memory of plain_kernel: push tile items, staging area and
-// the fused round's hash set with its first-position table.
+// the fused round's hash set with its first-position table and slot list.
 template <typename E>
 size_t plain_smem_bytes(uint32_t tile_log2) {
     const size_t tcap = std::max<size_t>(size_t(1) << tile_log2, kFuseDeg) + 2;
-    return (2 * tcap + 3 * (size_t)kStage) * sizeof(E) + 2 * (size_t)kHashSlots * sizeof(uint32_t);
+    return (2 * tcap + 3 * (size_t)kStage) * sizeof(E) + 2 * (size_t)kHashSlots * sizeof(uint32_t) +
+           (size_t)kFuseDeg * sizeof(uint16_t);
 }
 
 template <typename E, int BLOCK>
