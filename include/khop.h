@@ -372,6 +372,9 @@ int khop_graph_test_absent_cta(khop_graph *g, uint32_t barrier_index);
  * its frontier came out empty, so its count is final -- and admits waiting
  * requests into the free lanes, each with its own round counter: a request
  * that arrives while a traversal runs joins it at the next round boundary.
+ * Heavy requests of similar depth share a slot (one class for k = 3, one
+ * for k >= 4), so a slot's lanes mostly retire together.  While at most
+ * plain_heavy heavy requests wait, they take the single-query path instead.
  * Light requests (k <= 2) take a few microseconds each on the single-query
  * path, so plain slots answer them in arrival order, several per launch.
  * Slots (their device state) are admitted by free device memory and the
@@ -384,8 +387,10 @@ typedef struct khop_server khop_server;
 typedef struct {
     uint64_t mem_budget_bytes;   /* max device bytes for slot state (0 = no cap
                                     beyond free memory minus a 1 GiB margin)   */
-    uint32_t max_batches;        /* max rolling 64-lane slots per graph (0 = 2;
-                                    at most 2)                                   */
+    uint32_t max_batches;        /* max rolling 64-lane slots per graph (0 = 3;
+                                    at most 3).  Slots hold one depth class:
+                                    k = 3, or k >= 4; with 1 the single slot
+                                    takes both                                  */
     int64_t wait_timeout_us;     /* bound for the worker's wait for a step
                                     (0 = 2 s; negative: EINVAL)                 */
     uint32_t max_pending;        /* max queued requests before EBUSY (0 = 1<<20) */

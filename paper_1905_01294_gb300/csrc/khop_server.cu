@@ -15,7 +15,9 @@
 // at the next round boundary.  A retired lane is reused once its marks are
 // gone (see roll_kernel); when lanes run short the worker asks a step for a
 // clearing sweep.  Deep traversals share their large middle rounds this way,
-// so heavy slots are few (at most two per graph, max_batches permitting).
+// so heavy slots are few: at most three per graph (max_batches permitting),
+// each holding one depth class (k = 3, or k >= 4) so its lanes retire close
+// together.
 //
 // Light requests (k <= 2) cost a few microseconds each on the single-query
 // kernel, less than one round of a batch, so plain slots answer them in
