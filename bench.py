@@ -51,6 +51,22 @@ def workload_graph(scale: int):
 CHUNGLU = dict(n=41_600_000, edges=1_470_000_000, w_max=3e6, seed=4)
 
 
+def tune_graph(G, g):
+    """The launch configuration every leg times (and the full-size parity
+    tests check): the batched path's parameters tuned on 1024 seeds with k
+    mixed over {1,2,3,6}, like the batched leg; the plain path's grid shape,
+    push tile and direction parameters on 620 queries drawn like the paper
+    protocol, like the headline.  Both samples come from seed stream 9, not
+    the measured seeds.  Returns the khop_tuning in effect."""
+    tb = G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    s9, k9 = paper_queries(g, seed=9)
+    tp = G.autotune(s9, ks=k9)
+    G.set_tuning(direction=tp.direction, alpha=tp.alpha, beta=tp.beta, block_threads=tp.block_threads,
+                 blocks_per_sm=tp.blocks_per_sm, push_tile=tp.push_tile, batch_alpha=tb.batch_alpha,
+                 batch_beta=tb.batch_beta, batch_push_tile=tb.batch_push_tile)
+    return G.tuning()
+
+
 def workload(args):
     """(graph, workload name, batched query count)"""
     t0 = time.time()
@@ -64,10 +80,11 @@ def workload(args):
         time.time() - t0
 
 
-def paper_queries(g, scale_seeds=1.0):
-    """300/300/10/10 seeds (seed 2, uniform over out-degree > 0); the first
-    300 draws serve k = 1 and 2, the first 10 serve k = 3 and 6."""
-    s = gen.seeds(g, 300, seed=2)
+def paper_queries(g, scale_seeds=1.0, seed=2):
+    """300/300/10/10 seeds (seed stream 2 for the measured queries, uniform
+    over out-degree > 0); the first 300 draws serve k = 1 and 2, the first 10
+    serve k = 3 and 6."""
+    s = gen.seeds(g, 300, seed=seed)
     seeds, ks = [], []
     for k, cnt in PAPER_QUERIES:
         c = max(1, int(round(cnt * scale_seeds)))
@@ -455,6 +472,9 @@ def batched_leg(kh, torch, G, g, dev, stream, steps, warmup, flush, peak, nq=409
 K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
 
 
+SUSTAINED = 0.98   # a rate is sustained when this fraction of it is served
+
+
 def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
                 rates=(25e3, 50e3, 100e3, 150e3, 200e3, 300e3, 400e3), G2=None, g2=None, names=""):
     """Open-loop Poisson request stream (seed 3), k from {1:.4, 2:.3, 3:.2,
@@ -464,7 +484,9 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
     graph, a seeded fair coin sends each request to one of the two.
     Latency = completion time - scheduled arrival time.  `value` is the best
     achieved rate; latency is also reported at the highest offered rate the
-    server sustained."""
+    server sustained, i.e. served at >= SUSTAINED of the offered rate (at 0.9 a
+    rate whose queue still grows over the run passes, with a p50 of tens of
+    milliseconds)."""
     plain_rate = 1.0 / sum(p * plain_mean_us_by_k[k] * 1e-6 for k, p in K_MIX)
     points, checked = [], False
     for rate in rates:
@@ -533,7 +555,7 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
         if pt["achieved_qps"] < 0.9 * rate:
             break
     best = max(points, key=lambda x: x["achieved_qps"])
-    held = [p for p in points if p["achieved_qps"] >= 0.9 * p["offered_qps"]]
+    held = [p for p in points if p["achieved_qps"] >= SUSTAINED * p["offered_qps"]]
     top = max(held, key=lambda x: x["offered_qps"]) if held else None
     return {"workload": f"{names} resident, open-loop Poisson (seed 3), "
                         f"{nreq} requests per rate, k ~ {{1:.4, 2:.3, 3:.2, 6:.1}}",
@@ -806,7 +828,7 @@ def power_law_leg(args, kh, torch, dev, dist, world, rank, local, G2, g2):
     gl = gen.cached("chunglu", **CHUNGLU)
     t_gen = time.time() - t0
     GL = kh.Graph.from_csr(gl)
-    t = GL.autotune(gen.seeds(gl, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    t = tune_graph(GL, gl)
     tuning = {f: (getattr(t, f) if isinstance(getattr(t, f), int) else round(getattr(t, f), 3))
               for f, _ in t._fields_}
     name = (f"chunglu-n41.6M-m{gl.nnz}-wmax3e6-seed4 directed plain 300/300/10/10 seeds "
@@ -916,8 +938,7 @@ def main():
     nq = seeds.size
     G = kh.Graph.from_csr(g)
     if not args.case:
-        # tuning sample: 1024 seeds (seed 9, not the measured ones), k mixed over {1,2,3,6}
-        t = G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+        t = tune_graph(G, g)
         tuning = {f: (getattr(t, f) if isinstance(getattr(t, f), int) else round(getattr(t, f), 3))
                   for f, _ in t._fields_}
     if args.case == "mxv":

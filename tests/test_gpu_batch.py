@@ -143,11 +143,12 @@ def scale21_mixed():
 def test_scale21_mixed_workload_every_count_equals_the_oracle(scale21_mixed, mode):
     """All 4096 batched counts of the benchmark's batched leg equal the
     oracle's, at every lane width, in the tuning the benchmark times (the
-    graph autotuned on the benchmark's tuning sample); the plain path agrees
+    graph tuned as the benchmark tunes it, bench.tune_graph); the plain path agrees
     on the same queries."""
     g, G, seeds, ks, want = scale21_mixed
     if mode == kh.MODE_BATCHED64:
-        G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+        import bench
+        bench.tune_graph(G, g)
         plain = G.count_mixed(seeds, ks, mode=kh.MODE_PLAIN)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(kh.as_u64(plain), want)

@@ -1,7 +1,7 @@
 """Parity on the full-size power-law graph (41.6M vertices, 1.47e9 edges).
 
 This is the benchmark's Twitter-shaped workload, in the benchmark's launch
-configuration (the graph autotuned on the benchmark's tuning sample).  Every
+configuration (the graph tuned as the benchmark tunes it, bench.tune_graph).  Every
 count of the paper protocol (300/300/10/10 seeds at k = 1/2/3/6, one plain
 launch) and every count of the batched leg (1024 seeds, k mixed over
 {1,2,3,6}, 64 and 128 lanes per traversal) is compared with the oracle.
@@ -68,7 +68,7 @@ def test_chunglu_41M_every_count_equals_the_oracle():
     g = gen.cached("chunglu", **CHUNGLU)
     assert g.nnz >= 1_470_000_000 and g.n == 41_600_000
     G = kh.Graph.from_csr(g)
-    G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    bench.tune_graph(G, g)
     # the paper protocol, one plain launch: counts, TE and per-hop counts
     seeds, ks = bench.paper_queries(g)
     want_c, want_te, want_ph = oracle.khop_counts(g, seeds, ks, per_hop=True)

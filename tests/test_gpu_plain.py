@@ -305,14 +305,14 @@ def test_stats_are_consistent():
 def test_scale21_paper_protocol_in_bench_configuration():
     """The benchmark workload -- Kronecker scale 21, edge factor 16,
     symmetrized -- in the launch configuration the benchmark times: the
-    graph autotuned on the benchmark's tuning sample (1024 seeds of stream 9,
-    k mixed over {1,2,3,6}), then all 620 paper-protocol queries (300/300/10/10
+    graph tuned as the benchmark tunes it (bench.tune_graph: samples of seed
+    stream 9), then all 620 paper-protocol queries (300/300/10/10
     seeds at k = 1/2/3/6) in one khop_count_ex launch.  Every count, TE and
     per-hop count equals the oracle's."""
     import bench
     g = gen.rmat(21, 16, seed=1, symmetrize=True)
     G = kh.Graph.from_csr(g)
-    G.autotune(gen.seeds(g, 1024, seed=9), ks=gen.mixed_ks(1024, seed=9))
+    bench.tune_graph(G, g)
     seeds, ks = bench.paper_queries(g)
     assert seeds.size == 620
     want_c, want_te, want_ph = oracle.khop_counts(g, seeds, ks, per_hop=True)
