@@ -836,7 +836,7 @@ def power_law_leg(args, kh, torch, dev, dist, world, rank, local, G2, g2):
     sub = measure(args, kh, torch, dev, dist, world, rank, local, gl, GL, name, "chunglu", 1024,
                   tuning, min(args.steps, 5), min(args.warmup, 3),
                   serving_kw=None if args.no_serving else dict(
-                      G2=G2, g2=g2, nreq=20000, rates=(5e3, 10e3, 20e3, 40e3, 80e3, 160e3),
+                      G2=G2, g2=g2, nreq=20000, rates=(2.5e3, 5e3, 10e3, 20e3, 40e3, 80e3, 160e3),
                       names="chunglu-41.6M/1.47e9 and kronecker-s21"),
                   cpu_budget_s=10.0, directions=False, listing=False, pool_sample=64)
     sub["graph_load_s"] = t_gen
@@ -962,7 +962,7 @@ def main():
                    batched_nq, tuning, args.steps, args.warmup,
                    serving_kw=None if (args.no_extras or args.no_serving) else (
                        dict(names=wname.split(" ")[0]) if args.workload == "kronecker21" else
-                       dict(G2=None, names=wname.split(" ")[0], rates=(5e3, 10e3, 20e3, 40e3, 80e3))),
+                       dict(G2=None, names=wname.split(" ")[0], rates=(2.5e3, 5e3, 10e3, 20e3, 40e3, 80e3))),
                    directions=args.workload == "kronecker21",
                    pool_sample=512 if args.workload == "kronecker21" else 128)
     if args.workload == "kronecker21" and not args.no_extras and not args.no_large:
