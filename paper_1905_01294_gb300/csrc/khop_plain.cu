@@ -121,6 +121,10 @@ struct Shared {
     unsigned long long slot[4];  // counters of the round just finished
     unsigned m1;                 // fused round: distinct out-neighbours of the seed
     unsigned pdeg;               // row length of the prelude held in the hash tables
+    // the current query's result and stats, kept by thread 0 of CTA 0 only (in
+    // registers they would be live in every thread across the whole round loop)
+    unsigned long long q_count, q_te, q_bytes;
+    unsigned q_rounds, q_pull;
     uint64_t ring_q;             // thread 0: the query whose ring_advance is due next
     int flag;
 };
@@ -991,8 +995,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
         uint64_t mf = (uint64_t)(cur.re - cur.rs);   // out-edges of the frontier {s}
         uint64_t items = 1;
         uint64_t nf = 1;
-        uint64_t count = 0, te = 0, bytes = 0, sum_mf = 0, visited = 1;
-        uint32_t rounds = 0, pull_mask = 0;
+        uint64_t sum_mf = 0, visited = 1;
+        if (b0) {
+            sh.q_count = sh.q_te = sh.q_bytes = 0ull;
+            sh.q_rounds = sh.q_pull = 0u;
+        }
         int prev = DIR_PUSH;
         for (uint32_t r = 1; r <= k && mf > 0; ++r) {
             ++rdone;
@@ -1023,7 +1030,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
                 slots[kSlotWords * izero + 3] = 0ull;
                 slots[kSlotWords * izero + 4] = 0ull;
             }
-            te += mf;
+            if (b0) sh.q_te += mf;
             // Rounds 1 and 2 in one grid round (k >= 2, a push from a small seed
             // row): every CTA lists q_1 itself, so round 1 needs no barrier.
             // Not when Beamer's test would pull in round 2.
@@ -1120,17 +1127,19 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             if (fused) {
                 // rounds 1 and 2: q_1 (m1 vertices) was listed by every CTA
                 if (!do_pre) prelude_clear<BLOCK>(s_nbr, s_npos, s_pslot, sh);
-                bytes += 4ull * mf + (2ull * W + 4ull) + 4ull * m1;                   // round 1
-                bytes += 4ull * mf2 + (2ull * W + 4ull) * m1 + 4ull * items_out;      // round 2
-                te += mf2;
+                if (b0) {
+                    sh.q_bytes += 4ull * mf + (2ull * W + 4ull) + 4ull * m1;                   // round 1
+                    sh.q_bytes += 4ull * mf2 + (2ull * W + 4ull) * m1 + 4ull * items_out;      // round 2
+                    sh.q_te += mf2;
+                    sh.q_count += m1 + nnew;
+                    sh.q_rounds = 2u;
+                }
                 sum_mf += mf + mf2;
-                count += m1 + nnew;
                 visited += m1 + nnew;
                 nf = nnew;
                 items = qp >> a.ebits;
                 mf = R.last ? 0 : sh.slot[3];
                 prev = DIR_PUSH;
-                rounds = 2;
                 if (b0 && a.per_hop) {
                     if (a.hop_stride > 1) a.per_hop[q * a.hop_stride + 1] = m1;
                     if (a.hop_stride > 2) a.per_hop[q * a.hop_stride + 2] = nnew;
@@ -1143,35 +1152,37 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             // entries of the next); pull n/8 (visited sweep) + n/8 (next
             // frontier) + 2W per unvisited vertex with in-edges + 4 per in-edge
             // scanned.
-            if (dir == DIR_PUSH) {
-                bytes += 4ull * mf + (2ull * W + 4ull) * (r == 1 ? 1ull : items) + 4ull * items_out;
-            } else {
-                const uint64_t seen = visited + a.n_noin;
-                const uint64_t unvisited = a.n > seen ? a.n - seen : 0;
-                bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn;
+            if (b0) {
+                if (dir == DIR_PUSH) {
+                    sh.q_bytes += 4ull * mf + (2ull * W + 4ull) * (r == 1 ? 1ull : items) + 4ull * items_out;
+                } else {
+                    const uint64_t seen = visited + a.n_noin;
+                    const uint64_t unvisited = a.n > seen ? a.n - seen : 0;
+                    sh.q_bytes += 2ull * ((a.n + 7) / 8) + 2ull * W * unvisited + 4ull * scn;
+                }
+                sh.q_count += nnew;
+                sh.q_rounds = r;
+                if (dir == DIR_PULL && r <= 32) sh.q_pull |= 1u << (r - 1);
             }
             sum_mf += mf;
-            count += nnew;
             visited += nnew;
             nf = nnew;
             items = qp >> a.ebits;
             mf = R.last ? 0 : sh.slot[3];
             prev = dir;
-            rounds = r;
-            if (dir == DIR_PULL && r <= 32) pull_mask |= 1u << (r - 1);
             if (b0 && a.per_hop && r < a.hop_stride) a.per_hop[q * a.hop_stride + r] = nnew;
         }
         if (b0) {
             const uint64_t now = globaltimer_ns();
-            a.out[q] = count;
-            if (a.out_te) a.out_te[q] = te;
+            a.out[q] = sh.q_count;
+            if (a.out_te) a.out_te[q] = sh.q_te;
             if (a.stats) {
-                khop_query_stats st{t_prev, now, te, bytes, rounds, pull_mask};
+                khop_query_stats st{t_prev, now, sh.q_te, sh.q_bytes, sh.q_rounds, sh.q_pull};
                 a.stats[q] = st;
             }
             if (a.per_hop) {
                 if (a.hop_stride) a.per_hop[q * a.hop_stride] = 1ull;
-                for (uint64_t r = (uint64_t)rounds + 1; r < a.hop_stride; ++r)
+                for (uint64_t r = (uint64_t)sh.q_rounds + 1; r < a.hop_stride; ++r)
                     a.per_hop[q * a.hop_stride + r] = 0ull;
             }
             t_prev = now;
