@@ -837,16 +837,18 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
     const uint32_t s_first = cur.s;
     for (uint32_t i = threadIdx.x; i < kHashSlots; i += BLOCK) tab[i] = kHashEmpty;
     if (threadIdx.x == 0 && sh.ring_q != q) ring_restart(a, ring, q);   // else still in step
+    // the seed row of each query is loaded one query ahead (below), so its
+    // latency overlaps the previous query's bookkeeping
+    uint32_t w[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
+        w[u] = e < (uint32_t)(cur.re - cur.rs) ? a.ci[(uint64_t)cur.rs + e] : kHashEmpty;
+    }
     __syncthreads();
     for (uint64_t run = 1;; ++run) {
         if (threadIdx.x == 0) ring_advance(a, ring, q);
         const uint32_t deg = (uint32_t)(cur.re - cur.rs);
-        uint32_t w[kPer];
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
-            w[u] = e < deg ? a.ci[(uint64_t)cur.rs + e] : kHashEmpty;
-        }
         uint32_t slot[kPer];
         unsigned c = 0;
 #pragma unroll
@@ -860,6 +862,14 @@ __device__ __noinline__ void solo_run(const PlainArgs<E> &args, uint32_t *V, uin
         __syncthreads();   // counts complete; the ring's heads of q + 1, q + 2 published
         QueryHead<E> nxt{0u, 0u, (E)0, (E)0};
         const uint64_t qn = ring_next(a, ring, q, nxt);
+        if (qn < a.nq && solo_query(nxt, false)) {   // the next query's seed row, in flight from here
+            const uint32_t dn = (uint32_t)(nxt.re - nxt.rs);
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const uint32_t e = (uint32_t)(u * BLOCK) + threadIdx.x;
+                w[u] = e < dn ? a.ci[(uint64_t)nxt.rs + e] : kHashEmpty;
+            }
+        }
         if (threadIdx.x >= 32) ring_prefetch_row(a, ring, q + 2, threadIdx.x - 32u, BLOCK - 32u);
         if (threadIdx.x == 0) {
             const uint64_t cnt = sh.cnt;
