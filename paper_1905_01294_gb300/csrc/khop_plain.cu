@@ -106,6 +106,7 @@ struct Round {
     const uint32_t *nbr;     // fused: hash set of the seed's distinct out-neighbours
     uint32_t level;          // the round's number (its discoveries are at that hop distance)
     uint32_t rot;            // rotation of the push tiles over CTAs 1 .. G-1 (same in every CTA)
+    uint32_t tl;             // log2 of the push tile (fused rounds: sized to the round)
 };
 
 // Per-CTA shared state of a round.
@@ -305,7 +306,7 @@ __device__ __forceinline__ void flush_round(const PlainArgs<E> &a, const Round<E
 template <typename E, int BLOCK>
 __device__ __forceinline__ void push_round(const PlainArgs<E> &a, const Round<E> &R, E *s_pre,
                                            E *s_rs, Shared &sh, E *st_pre, E *st_rs, E *st_d) {
-    const uint32_t tl = a.tile_log2;
+    const uint32_t tl = R.tl;
     const uint64_t T = 1ull << tl;
     const uint64_t ntiles = (R.mf + T - 1) >> tl;
     // CTA 0 writes the query results between queries: it takes tile G - 1.
@@ -1077,6 +1078,13 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) plain_kernel(const PlainA
             R.nbr = s_nbr;
             R.level = fused ? 2u : r;
             R.rot = rot;
+            // A fused round's items are in every CTA's shared memory, so its
+            // tiles need no tile map: they grow to about m_f / G edges, so
+            // that each CTA's passes of BLOCK * kPushUnroll edges run full
+            // (fixed tiles of T < BLOCK * kPushUnroll leave slots empty).
+            R.tl = a.tile_log2;
+            if (fused)
+                while (R.tl < 24u && ((uint64_t)gridDim.x << R.tl) < mf2) ++R.tl;
             R.seed = s;
             R.seed_rs = cur.rs;
             R.V = V;
