@@ -34,7 +34,7 @@ constexpr uint32_t kFuseDeg = 1024;          // seeds with at most this many out
                                              // a larger row makes the prelude L2-bound)
 constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 1/32 of the
                                              // vertices are visited) read V before test-and-set
-constexpr int kPullWords = 2;    // bitmap words a warp works on at once in a pull round
+constexpr int kListWords = 16;   // bitmap words whose unvisited vertices a warp lists at once (pull)
 constexpr int kFlatILP = 2;      // in-edges per lane per step of the flattened pull scan
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
 constexpr int kStagePosShift = 40;                       // staged count above, edges below
@@ -510,21 +510,22 @@ __device__ __forceinline__ void prelude_clear(uint32_t *tab, uint32_t *pos, cons
     }
 }
 
-// Pull round (masked SpMV over the unvisited vertices).  Warp w owns the
-// bitmap words w * P + m * S + j (P = kPullWords, S = P * warps of the grid,
-// j < P, m = 0, 1, ...).  It first loads the visited and in-edge-less words
-// of 32 of them at once (one per lane) and keeps only the open words -- those
-// with a vertex that is unvisited and has in-edges -- so closed words cost no
-// dependent round trip (late rounds of a deep query are mostly closed).  The
-// open words are then worked kPullWords at a time (lane l owns vertex 32 i + l
-// of word i), so their loads are in flight together.  Every unvisited vertex
-// first checks its first two in-edges against the frontier bitmap; the
-// in-edges of the vertices still unresolved are then scanned word by word as
-// one flattened list: the warp takes the next 32 * kFlatILP edges of the
-// concatenated remaining in-edge lists (a load-balanced search over the
-// lanes' remaining counts), and a vertex drops out as soon as one of its
-// in-neighbours is in the frontier.  The output bitmap F_out was zeroed one
-// round ahead, so only words with a discovery are written.
+// Pull round (masked SpMV over the unvisited vertices).  Warps take groups
+// of kListWords consecutive bitmap words (one per lane, grid-strided) and
+// list the group's unvisited vertices with in-edges -- V OR the in-edge-less
+// bitmap, complemented -- by a warp scan of the words' popcounts; the list is
+// then worked 32 vertices at a time, one per lane (its word by a shuffle
+// search over the scan, its bit by __fns), so every lane has a vertex
+// whether the unvisited vertices are dense (early rounds) or one or two per
+// word (late rounds of a deep query).  Each vertex first checks its first two
+// in-edges against the frontier bitmap; the in-edges of the vertices still
+// unresolved are then scanned as one flattened list: the warp takes the next
+// 32 * kFlatILP edges of the concatenated remaining in-edge lists (a
+// load-balanced search over the lanes' remaining counts), and a vertex drops
+// out as soon as one of its in-neighbours is in the frontier.  A found vertex
+// is marked in V, and (through record) in F_out if it has out-edges -- a
+// later pull looks for parents, and a parent has an out-edge; F_out was
+// zeroed one round ahead.
 template <typename E, int BLOCK>
 __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E> &R, Shared &sh,
                                            E *s_winc, E *s_wpos, E *st_pre, E *st_rs, E *st_d) {
@@ -533,125 +534,88 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
     E *wpos = s_wpos + (threadIdx.x >> 5) * 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * BLOCK) >> 5;
-    const uint64_t S = nwarps * kPullWords;                 // stride between a warp's word groups
-    constexpr int kGroups = 32 / kPullWords;                // word groups looked at per batch
     const uint32_t tail_open = (a.n & 31) ? ~(~0u << (a.n & 31)) : ~0u;   // valid bits of the last word
     uint64_t scanned = 0;
-    for (uint64_t c0 = gwarp * kPullWords; c0 < a.nw; c0 += S * kGroups) {
-        // lane l looks at word c0 + (l / P) * S + l % P: closed words are skipped
-        const uint64_t il = c0 + (uint64_t)(lane / kPullWords) * S + (uint64_t)(lane % kPullWords);
+    for (uint64_t c0 = gwarp * kListWords; c0 < a.nw; c0 += nwarps * kListWords) {
+        const uint64_t il = c0 + (uint64_t)lane;
         uint32_t wl = ~0u;
-        if (il < a.nw) {
+        if (lane < kListWords && il < a.nw) {
             wl = R.V[il] | a.noin[il];
             if (il == a.nw - 1) wl |= ~tail_open;
         }
-        unsigned open = __ballot_sync(FULL, wl != ~0u);
-        // word looked at by lane L (closed bits of wl include those past n)
-        const auto word_of = [&](int L) {
-            return c0 + (uint64_t)(L / kPullWords) * S + (uint64_t)(L % kPullWords);
-        };
-        while (open) {
-            int Lw[kPullWords];   // lane holding the j-th open word of this step, or -1
-            bool unv[kPullWords], found[kPullWords];
+        const uint32_t fr = ~wl;   // this lane's word: unvisited vertices with in-edges
+        const uint32_t cnt = (uint32_t)__popc(fr);
+        const uint32_t incl = warp_inclusive_sum(cnt);
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t x = base + (uint32_t)lane;   // this lane's list position
+            int L = 0;                                   // first lane whose inclusive count exceeds x
 #pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                Lw[j] = open ? __ffs(open) - 1 : -1;
-                open &= open - 1u;
-                const uint32_t w = __shfl_sync(FULL, wl, Lw[j] < 0 ? 0 : Lw[j]);
-                unv[j] = Lw[j] >= 0 && !((w >> lane) & 1u);
-                found[j] = false;
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t im = __shfl_sync(FULL, incl, L + step - 1);
+                if (im <= x) L += step;
             }
-            E b[kPullWords], e[kPullWords], pos[kPullWords];
-#pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                b[j] = 0;
-                e[j] = 0;
-                if (unv[j]) {
-                    const uint64_t v = (word_of(Lw[j]) << 5) + (uint64_t)lane;
-                    b[j] = a.cp[v];
-                    e[j] = a.cp[v + 1];
-                }
-                pos[j] = b[j];
+            const bool unv = x < total;
+            L = min(L, 31);
+            const uint32_t fro = __shfl_sync(FULL, fr, L);
+            const uint32_t exo = __shfl_sync(FULL, incl - cnt, L);
+            const uint32_t bit = unv ? __fns(fro, 0u, (int)(x - exo) + 1) : 0u;
+            const uint64_t v = ((c0 + (uint64_t)L) << 5) + (uint64_t)bit;
+            E b = 0, e = 0;
+            if (unv) {
+                b = a.cp[v];
+                e = a.cp[v + 1];
             }
-            uint32_t u0[kPullWords], u1[kPullWords];
-            bool l0[kPullWords], l1[kPullWords];
+            E pos = b;
+            const bool l0 = unv && pos < e;
+            const bool l1 = l0 && pos + 1 < e;
+            const uint32_t u0 = l0 ? a.ri[pos] : 0u;
+            const uint32_t u1 = l1 ? a.ri[pos + 1] : 0u;
+            bool found = l0 && ((R.Fin[u0 >> 5] >> (u0 & 31)) & 1u);
+            found = found || (l1 && ((R.Fin[u1 >> 5] >> (u1 & 31)) & 1u));
+            pos += (E)l0 + (E)l1;
+            scanned += (uint64_t)l0 + (uint64_t)l1;
+            E rem = (unv && !found) ? e - pos : (E)0;
+            while (__any_sync(FULL, rem > 0)) {
+                const E inc2 = warp_inclusive_sum(rem);
+                const E tot2 = __shfl_sync(FULL, inc2, 31);
+                const E exc2 = inc2 - rem;
+                winc[lane] = inc2;
+                wpos[lane] = pos - exc2;
+                __syncwarp();
+                const uint32_t chunk = (uint32_t)min(tot2, (E)(32 * kFlatILP));
+                unsigned hits = 0;
 #pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                l0[j] = unv[j] && pos[j] < e[j];
-                l1[j] = l0[j] && pos[j] + 1 < e[j];
-                u0[j] = l0[j] ? a.ri[pos[j]] : 0u;
-                u1[j] = l1[j] ? a.ri[pos[j] + 1] : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                bool h = l0[j] && ((R.Fin[u0[j] >> 5] >> (u0[j] & 31)) & 1u);
-                h = h || (l1[j] && ((R.Fin[u1[j] >> 5] >> (u1[j] & 31)) & 1u));
-                found[j] = h;
-                pos[j] += (E)l0[j] + (E)l1[j];
-                scanned += (uint64_t)l0[j] + (uint64_t)l1[j];
-            }
-#pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                E rem = (unv[j] && !found[j]) ? e[j] - pos[j] : (E)0;
-                while (__any_sync(FULL, rem > 0)) {
-                    const E incl = warp_inclusive_sum(rem);
-                    const E total = __shfl_sync(FULL, incl, 31);
-                    const E excl = incl - rem;
-                    winc[lane] = incl;
-                    wpos[lane] = pos[j] - excl;   // edge of flat index x owned by lane L: wpos[L] + x
-                    __syncwarp();
-                    const uint32_t chunk = (uint32_t)min(total, (E)(32 * kFlatILP));
-                    uint32_t uu[kFlatILP];
-                    int own[kFlatILP];
-#pragma unroll
-                    for (int t = 0; t < kFlatILP; ++t) {
-                        const uint32_t x = (uint32_t)(t * 32 + lane);
-                        own[t] = -1;
-                        uu[t] = 0;
-                        if (x < chunk) {
-                            int lo = 0, hi = 31;   // first lane whose inclusive count exceeds x
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (winc[mid] > (E)x) hi = mid; else lo = mid + 1;
-                            }
-                            own[t] = lo;
-                            uu[t] = a.ri[wpos[lo] + (E)x];
+                for (int t = 0; t < kFlatILP; ++t) {
+                    const uint32_t xx = (uint32_t)(t * 32 + lane);
+                    if (xx < chunk) {
+                        int lo = 0, hi = 31;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (winc[mid] > (E)xx) hi = mid; else lo = mid + 1;
                         }
+                        const uint32_t uu = a.ri[wpos[lo] + (E)xx];
+                        if ((R.Fin[uu >> 5] >> (uu & 31)) & 1u) hits |= 1u << lo;
                     }
-                    unsigned hits = 0;
-#pragma unroll
-                    for (int t = 0; t < kFlatILP; ++t)
-                        if (own[t] >= 0 && ((R.Fin[uu[t] >> 5] >> (uu[t] & 31)) & 1u))
-                            hits |= 1u << own[t];
-                    hits = __reduce_or_sync(FULL, hits);
-                    const E consumed = (E)chunk > excl ? min(rem, (E)chunk - excl) : (E)0;
-                    pos[j] += consumed;
-                    rem -= consumed;
-                    if ((hits >> lane) & 1u) {
-                        found[j] = true;
-                        rem = 0;
-                    }
-                    if (lane == 0) scanned += chunk;
-                    __syncwarp();
                 }
+                hits = __reduce_or_sync(FULL, hits);
+                const E consumed = (E)chunk > exc2 ? min(rem, (E)chunk - exc2) : (E)0;
+                pos += consumed;
+                rem -= consumed;
+                if ((hits >> lane) & 1u) {
+                    found = true;
+                    rem = 0;
+                }
+                if (lane == 0) scanned += chunk;
+                __syncwarp();
             }
-#pragma unroll
-            for (int j = 0; j < kPullWords; ++j) {
-                if (Lw[j] < 0) break;   // warp-uniform
-                const uint64_t i = word_of(Lw[j]);
-                const unsigned nm = __ballot_sync(FULL, found[j]);
-                if (lane == 0 && nm) {
-                    R.Fout[i] = nm;
-                    atomicOr(&R.V[i], nm);   // V keeps traversal marks only (no in-edge-less bits)
-                }
-                const uint64_t v = (i << 5) + (uint64_t)lane;
-                E rs = 0, d = 0;
-                if (found[j] && !R.last) {
-                    if (a.symmetric) { rs = b[j]; d = e[j] - b[j]; }
-                    else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
-                }
-                record(a, R, found[j], (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
+            if (found) atomicOr(&R.V[v >> 5], 1u << (v & 31));
+            E rs = 0, d = 0;
+            if (found && !R.last) {
+                if (a.symmetric) { rs = b; d = e - b; }
+                else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
             }
+            record(a, R, found, (uint32_t)v, rs, d, true, sh, st_pre, st_rs, st_d);
         }
     }
     scanned = warp_sum(scanned);
