@@ -522,10 +522,9 @@ __device__ __forceinline__ void prelude_clear(uint32_t *tab, uint32_t *pos, cons
 // unresolved are then scanned as one flattened list: the warp takes the next
 // 32 * kFlatILP edges of the concatenated remaining in-edge lists (a
 // load-balanced search over the lanes' remaining counts), and a vertex drops
-// out as soon as one of its in-neighbours is in the frontier.  A found vertex
-// is marked in V, and (through record) in F_out if it has out-edges -- a
-// later pull looks for parents, and a parent has an out-edge; F_out was
-// zeroed one round ahead.
+// out as soon as one of its in-neighbours is in the frontier.  Found
+// vertices are marked in V and F_out with one reduction per bitmap word (F_out
+// was zeroed one round ahead).
 template <typename E, int BLOCK>
 __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E> &R, Shared &sh,
                                            E *s_winc, E *s_wpos, E *st_pre, E *st_rs, E *st_d) {
@@ -609,13 +608,30 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
                 if (lane == 0) scanned += chunk;
                 __syncwarp();
             }
-            if (found) atomicOr(&R.V[v >> 5], 1u << (v & 31));
+            // The list runs in vertex order, so lanes holding the same word are
+            // consecutive: a segmented OR-scan gives the last lane of each run
+            // the run's found bits, and it alone marks them in V and F_out.
+            {
+                const uint32_t wv = unv ? (uint32_t)(v >> 5) : 0xffffffffu;
+                uint32_t acc = found ? 1u << (v & 31) : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, acc, o);
+                    const uint32_t yw = __shfl_up_sync(FULL, wv, o);
+                    if (lane >= o && yw == wv) acc |= y;
+                }
+                const uint32_t nw = __shfl_down_sync(FULL, wv, 1);
+                if (acc && (lane == 31 || nw != wv)) {
+                    atomicOr(&R.V[wv], acc);
+                    if (!R.last) atomicOr(&R.Fout[wv], acc);
+                }
+            }
             E rs = 0, d = 0;
             if (found && !R.last) {
                 if (a.symmetric) { rs = b; d = e - b; }
                 else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
             }
-            record(a, R, found, (uint32_t)v, rs, d, true, sh, st_pre, st_rs, st_d);
+            record(a, R, found, (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
         }
     }
     scanned = warp_sum(scanned);
