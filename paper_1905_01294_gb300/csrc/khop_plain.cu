@@ -36,6 +36,7 @@ constexpr uint64_t kPrecheckEdges = 16384;   // push rounds this big (once over 
                                              // vertices are visited) read V before test-and-set
 constexpr int kListWords = 16;   // bitmap words whose unvisited vertices a warp lists at once (pull)
 constexpr int kFlatILP = 2;      // in-edges per lane per step of the flattened pull scan
+constexpr int kListILP = 2;      // listed vertices per lane per step (their first in-edges in flight)
 constexpr int kStage = 2048;     // queue items a CTA stages in shared memory per round
 constexpr int kStagePosShift = 40;                       // staged count above, edges below
 constexpr unsigned long long kStageEdgeMask = (1ull << kStagePosShift) - 1ull;
@@ -515,7 +516,8 @@ __device__ __forceinline__ void prelude_clear(uint32_t *tab, uint32_t *pos, cons
 // list the group's unvisited vertices with in-edges -- V OR the in-edge-less
 // bitmap, complemented -- by a warp scan of the words' popcounts; the list is
 // then worked 32 vertices at a time, one per lane (its word by a shuffle
-// search over the scan, its bit by __fns), so every lane has a vertex
+// search over the scan, its bit by __fns; kListILP vertices per lane, their
+// first in-edges in flight together), so every lane has a vertex
 // whether the unvisited vertices are dense (early rounds) or one or two per
 // word (late rounds of a deep query).  Each vertex first checks its first two
 // in-edges against the frontier bitmap; the in-edges of the vertices still
@@ -546,92 +548,117 @@ __device__ __forceinline__ void pull_round(const PlainArgs<E> &a, const Round<E>
         const uint32_t cnt = (uint32_t)__popc(fr);
         const uint32_t incl = warp_inclusive_sum(cnt);
         const uint32_t total = __shfl_sync(FULL, incl, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t x = base + (uint32_t)lane;   // this lane's list position
-            int L = 0;                                   // first lane whose inclusive count exceeds x
+        for (uint32_t base = 0; base < total; base += 32 * kListILP) {
+            // lane l takes list positions base + j * 32 + l (j < kListILP): their
+            // first in-edges are loaded and checked together
+            uint64_t v[kListILP];
+            E b[kListILP], e[kListILP], pos[kListILP];
+            bool unv[kListILP], found[kListILP];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t im = __shfl_sync(FULL, incl, L + step - 1);
-                if (im <= x) L += step;
-            }
-            const bool unv = x < total;
-            L = min(L, 31);
-            const uint32_t fro = __shfl_sync(FULL, fr, L);
-            const uint32_t exo = __shfl_sync(FULL, incl - cnt, L);
-            const uint32_t bit = unv ? __fns(fro, 0u, (int)(x - exo) + 1) : 0u;
-            const uint64_t v = ((c0 + (uint64_t)L) << 5) + (uint64_t)bit;
-            E b = 0, e = 0;
-            if (unv) {
-                b = a.cp[v];
-                e = a.cp[v + 1];
-            }
-            E pos = b;
-            const bool l0 = unv && pos < e;
-            const bool l1 = l0 && pos + 1 < e;
-            const uint32_t u0 = l0 ? a.ri[pos] : 0u;
-            const uint32_t u1 = l1 ? a.ri[pos + 1] : 0u;
-            bool found = l0 && ((R.Fin[u0 >> 5] >> (u0 & 31)) & 1u);
-            found = found || (l1 && ((R.Fin[u1 >> 5] >> (u1 & 31)) & 1u));
-            pos += (E)l0 + (E)l1;
-            scanned += (uint64_t)l0 + (uint64_t)l1;
-            E rem = (unv && !found) ? e - pos : (E)0;
-            while (__any_sync(FULL, rem > 0)) {
-                const E inc2 = warp_inclusive_sum(rem);
-                const E tot2 = __shfl_sync(FULL, inc2, 31);
-                const E exc2 = inc2 - rem;
-                winc[lane] = inc2;
-                wpos[lane] = pos - exc2;
-                __syncwarp();
-                const uint32_t chunk = (uint32_t)min(tot2, (E)(32 * kFlatILP));
-                unsigned hits = 0;
+            for (int j = 0; j < kListILP; ++j) {
+                const uint32_t x = base + (uint32_t)(j * 32 + lane);
+                int L = 0;                                   // first lane whose inclusive count exceeds x
 #pragma unroll
-                for (int t = 0; t < kFlatILP; ++t) {
-                    const uint32_t xx = (uint32_t)(t * 32 + lane);
-                    if (xx < chunk) {
-                        int lo = 0, hi = 31;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (winc[mid] > (E)xx) hi = mid; else lo = mid + 1;
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t im = __shfl_sync(FULL, incl, L + step - 1);
+                    if (im <= x) L += step;
+                }
+                unv[j] = x < total;
+                L = min(L, 31);
+                const uint32_t fro = __shfl_sync(FULL, fr, L);
+                const uint32_t exo = __shfl_sync(FULL, incl - cnt, L);
+                const uint32_t bit = unv[j] ? __fns(fro, 0u, (int)(x - exo) + 1) : 0u;
+                v[j] = ((c0 + (uint64_t)L) << 5) + (uint64_t)bit;
+                b[j] = 0;
+                e[j] = 0;
+                if (unv[j]) {
+                    b[j] = a.cp[v[j]];
+                    e[j] = a.cp[v[j] + 1];
+                }
+                pos[j] = b[j];
+            }
+            uint32_t u0[kListILP], u1[kListILP];
+            bool l0[kListILP], l1[kListILP];
+#pragma unroll
+            for (int j = 0; j < kListILP; ++j) {
+                l0[j] = unv[j] && pos[j] < e[j];
+                l1[j] = l0[j] && pos[j] + 1 < e[j];
+                u0[j] = l0[j] ? a.ri[pos[j]] : 0u;
+                u1[j] = l1[j] ? a.ri[pos[j] + 1] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < kListILP; ++j) {
+                bool f = l0[j] && ((R.Fin[u0[j] >> 5] >> (u0[j] & 31)) & 1u);
+                f = f || (l1[j] && ((R.Fin[u1[j] >> 5] >> (u1[j] & 31)) & 1u));
+                found[j] = f;
+                pos[j] += (E)l0[j] + (E)l1[j];
+                scanned += (uint64_t)l0[j] + (uint64_t)l1[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kListILP; ++j) {
+                E rem = (unv[j] && !found[j]) ? e[j] - pos[j] : (E)0;
+                while (__any_sync(FULL, rem > 0)) {
+                    const E inc2 = warp_inclusive_sum(rem);
+                    const E tot2 = __shfl_sync(FULL, inc2, 31);
+                    const E exc2 = inc2 - rem;
+                    winc[lane] = inc2;
+                    wpos[lane] = pos[j] - exc2;
+                    __syncwarp();
+                    const uint32_t chunk = (uint32_t)min(tot2, (E)(32 * kFlatILP));
+                    unsigned hits = 0;
+#pragma unroll
+                    for (int t = 0; t < kFlatILP; ++t) {
+                        const uint32_t xx = (uint32_t)(t * 32 + lane);
+                        if (xx < chunk) {
+                            int lo = 0, hi = 31;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (winc[mid] > (E)xx) hi = mid; else lo = mid + 1;
+                            }
+                            const uint32_t uu = a.ri[wpos[lo] + (E)xx];
+                            if ((R.Fin[uu >> 5] >> (uu & 31)) & 1u) hits |= 1u << lo;
                         }
-                        const uint32_t uu = a.ri[wpos[lo] + (E)xx];
-                        if ((R.Fin[uu >> 5] >> (uu & 31)) & 1u) hits |= 1u << lo;
+                    }
+                    hits = __reduce_or_sync(FULL, hits);
+                    const E consumed = (E)chunk > exc2 ? min(rem, (E)chunk - exc2) : (E)0;
+                    pos[j] += consumed;
+                    rem -= consumed;
+                    if ((hits >> lane) & 1u) {
+                        found[j] = true;
+                        rem = 0;
+                    }
+                    if (lane == 0) scanned += chunk;
+                    __syncwarp();
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kListILP; ++j) {
+                // The list runs in vertex order, so lanes holding the same word
+                // are consecutive: a segmented OR-scan gives the last lane of
+                // each run the run's found bits, and it alone marks them in V
+                // and F_out.
+                {
+                    const uint32_t wv = unv[j] ? (uint32_t)(v[j] >> 5) : 0xffffffffu;
+                    uint32_t acc = found[j] ? 1u << (v[j] & 31) : 0u;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, acc, o);
+                        const uint32_t yw = __shfl_up_sync(FULL, wv, o);
+                        if (lane >= o && yw == wv) acc |= y;
+                    }
+                    const uint32_t nw = __shfl_down_sync(FULL, wv, 1);
+                    if (acc && (lane == 31 || nw != wv)) {
+                        atomicOr(&R.V[wv], acc);
+                        if (!R.last) atomicOr(&R.Fout[wv], acc);
                     }
                 }
-                hits = __reduce_or_sync(FULL, hits);
-                const E consumed = (E)chunk > exc2 ? min(rem, (E)chunk - exc2) : (E)0;
-                pos += consumed;
-                rem -= consumed;
-                if ((hits >> lane) & 1u) {
-                    found = true;
-                    rem = 0;
+                E rs = 0, d = 0;
+                if (found[j] && !R.last) {
+                    if (a.symmetric) { rs = b[j]; d = e[j] - b[j]; }
+                    else { rs = a.rp[v[j]]; d = a.rp[v[j] + 1] - rs; }
                 }
-                if (lane == 0) scanned += chunk;
-                __syncwarp();
+                record(a, R, found[j], (uint32_t)v[j], rs, d, false, sh, st_pre, st_rs, st_d);
             }
-            // The list runs in vertex order, so lanes holding the same word are
-            // consecutive: a segmented OR-scan gives the last lane of each run
-            // the run's found bits, and it alone marks them in V and F_out.
-            {
-                const uint32_t wv = unv ? (uint32_t)(v >> 5) : 0xffffffffu;
-                uint32_t acc = found ? 1u << (v & 31) : 0u;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(FULL, acc, o);
-                    const uint32_t yw = __shfl_up_sync(FULL, wv, o);
-                    if (lane >= o && yw == wv) acc |= y;
-                }
-                const uint32_t nw = __shfl_down_sync(FULL, wv, 1);
-                if (acc && (lane == 31 || nw != wv)) {
-                    atomicOr(&R.V[wv], acc);
-                    if (!R.last) atomicOr(&R.Fout[wv], acc);
-                }
-            }
-            E rs = 0, d = 0;
-            if (found && !R.last) {
-                if (a.symmetric) { rs = b; d = e - b; }
-                else { rs = a.rp[v]; d = a.rp[v + 1] - rs; }
-            }
-            record(a, R, found, (uint32_t)v, rs, d, false, sh, st_pre, st_rs, st_d);
         }
     }
     scanned = warp_sum(scanned);
