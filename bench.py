@@ -475,6 +475,14 @@ K_MIX = ((1, 0.4), (2, 0.3), (3, 0.2), (6, 0.1))
 SUSTAINED = 0.98   # a rate is sustained when this fraction of it is served
 
 
+def best_and_sustained(points):
+    """The sweep point with the highest achieved rate, and the one with the
+    highest offered rate that was sustained (None if none was)."""
+    best = max(points, key=lambda x: x["achieved_qps"])
+    held = [p for p in points if p["achieved_qps"] >= SUSTAINED * p["offered_qps"]]
+    return best, (max(held, key=lambda x: x["offered_qps"]) if held else None)
+
+
 def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
                 rates=(25e3, 50e3, 100e3, 150e3, 200e3, 300e3, 400e3), G2=None, g2=None, names=""):
     """Open-loop Poisson request stream (seed 3), k from {1:.4, 2:.3, 3:.2,
@@ -554,9 +562,7 @@ def serving_leg(kh, G, g, plain_mean_us_by_k, nreq=100000,
         points.append(pt)
         if pt["achieved_qps"] < 0.9 * rate:
             break
-    best = max(points, key=lambda x: x["achieved_qps"])
-    held = [p for p in points if p["achieved_qps"] >= SUSTAINED * p["offered_qps"]]
-    top = max(held, key=lambda x: x["offered_qps"]) if held else None
+    best, top = best_and_sustained(points)
     return {"workload": f"{names} resident, open-loop Poisson (seed 3), "
                         f"{nreq} requests per rate, k ~ {{1:.4, 2:.3, 3:.2, 6:.1}}",
             "value": best["achieved_qps"], "unit": "queries/s",
